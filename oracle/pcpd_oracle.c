@@ -1,0 +1,404 @@
+/*
+ * pcpd_oracle.c -- plain, slow, scalar CPU oracle for the bit-sliced PCPD sweep.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may call, link or load this
+ * file: only the tests, __graft_entry__.smoke() and bench.py's CPU-baseline leg use it.
+ * It shares no code, header, table or constant generator with the CUDA library.
+ *
+ * What it computes (the paper: Schram, arXiv 1301.6082):
+ *   - the PCPD reactions of Eq. (1) with the bond-level decision tree of Alg. 1 (Sec. 2);
+ *   - on the parallel schedule of non-overlapping 3-site windows with a random phase per
+ *     sub-step (the reading of Sec. 3's "same local site" schedule that this project uses);
+ *   - with one rate draw u per sample and window, compared with integer thresholds
+ *     floor(rate * 2^32), the exact generalisation of the dyadic masks of Sec. 4.2-4.3;
+ *   - random bits from Philox4x32-10 (Salmon et al., SC'11), keyed by seed and counted by
+ *     (window, sub-step, group, tag|block);
+ *   - and, separately, Alg. 1 itself (random-sequential updates) as a statistical reference.
+ *
+ * Every sample is simulated one at a time on a byte per site.  All 32 bit planes of u are
+ * always computed (no early exit).  Parallelism over 32-sample groups with pthreads only
+ * splits independent work; it changes no arithmetic and integer sums are order-free.
+ *
+ * Pins: every function is checked in tests/test_oracle_*.py against something other than
+ * itself (a third-party Philox, closed forms, invariants, exact master equations).
+ * Build: gcc -O2 -ffp-contract=off -fPIC -shared -pthread (see oracle/oracle.py).
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_TAG_DYN 0u
+#define ORC_TAG_PHASE 1u
+#define ORC_TAG_INIT 2u
+#define ORC_TAG_RS 3u
+#define ORC_TWO32 4294967296ull
+
+/* ---------------------------------------------------------------------------------------
+ * Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3",
+ * SC'11).  One round: (x0,x1,x2,x3) -> (hi(M1*x2)^x1^k0, lo(M1*x2), hi(M0*x0)^x3^k1,
+ * lo(M0*x0)); the key is bumped by the Weyl constants after every round; ten rounds.
+ * ------------------------------------------------------------------------------------- */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t prod0 = (uint64_t)0xD2511F53u * (uint64_t)x0;
+        uint64_t prod1 = (uint64_t)0xCD9E8D57u * (uint64_t)x2;
+        uint32_t y0 = (uint32_t)(prod1 >> 32) ^ x1 ^ k0;
+        uint32_t y1 = (uint32_t)prod1;
+        uint32_t y2 = (uint32_t)(prod0 >> 32) ^ x3 ^ k1;
+        uint32_t y3 = (uint32_t)prod0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+static void orc_block(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                      uint32_t out[4])
+{
+    uint32_t ctr[4] = {c0, c1, c2, c3};
+    uint32_t key[2] = {(uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32)};
+    orc_philox4x32_10(ctr, key, out);
+}
+
+/* Batch form for tests: n counters (row-major [n][4]) -> n outputs [n][4]. */
+void orc_philox_batch(const uint32_t *ctrs, uint64_t seed, uint32_t *outs, uint64_t n)
+{
+    for (uint64_t i = 0; i < n; ++i)
+        orc_block(seed, ctrs[4 * i], ctrs[4 * i + 1], ctrs[4 * i + 2], ctrs[4 * i + 3],
+                  outs + 4 * i);
+}
+
+/* ---------------------------------------------------------------------------------------
+ * Thresholds, the integer form of the rates of Eq. (1): P(diffuse) = d, P(annihilate) =
+ * p(1-d), P(fission) = (1-p)(1-d).  Double precision, evaluated exactly as written, no
+ * contraction: T_D = min(2^32, floor(d*2^32)), T_A = floor(p*(1-d)*2^32),
+ * T_DA = min(2^32, T_D + T_A).  Random-sequential form (Alg. 1): T_P = min(2^32, floor(p*2^32)).
+ * ------------------------------------------------------------------------------------- */
+static uint64_t orc_floor_scaled(double x)
+{
+    double f = floor(x);
+    if (f <= 0.0) return 0;
+    if (f >= 4294967296.0) return ORC_TWO32;
+    return (uint64_t)f;
+}
+
+int orc_thresholds(double p, double d, uint64_t *t_d, uint64_t *t_da, uint64_t *t_p)
+{
+    if (!(p >= 0.0 && p <= 1.0 && d >= 0.0 && d <= 1.0)) return 1;
+    uint64_t td = orc_floor_scaled(d * 4294967296.0);
+    double scaled_a = p * (1.0 - d);
+    scaled_a = scaled_a * 4294967296.0;
+    uint64_t ta = orc_floor_scaled(scaled_a);
+    uint64_t tda = td + ta;
+    if (tda > ORC_TWO32) tda = ORC_TWO32;
+    if (t_d) *t_d = td;
+    if (t_da) *t_da = tda;
+    if (t_p) *t_p = orc_floor_scaled(p * 4294967296.0);
+    return 0;
+}
+
+/* Time: after n sub-steps a sample has had n*K attempts, K = floor(L/3); MCS time t
+ * (t*L attempts) is reached at sub-step ceil(t*L/K). */
+uint64_t orc_substep_of_time(uint32_t L, uint64_t t)
+{
+    unsigned __int128 K = L / 3u;
+    unsigned __int128 num = (unsigned __int128)t * L;
+    return (uint64_t)((num + K - 1) / K);
+}
+
+/* Random phase of sub-step n for phase group h: phi = floor(x0 * L / 2^32). */
+uint32_t orc_phase(uint64_t seed, uint32_t L, uint32_t h, uint32_t n)
+{
+    uint32_t out[4];
+    orc_block(seed, 0u, n, h, ORC_TAG_PHASE << 28, out);
+    return (uint32_t)(((uint64_t)out[0] * (uint64_t)L) >> 32);
+}
+
+/* ---------------------------------------------------------------------------------------
+ * Lattice state of the oracle: one byte per (sample, site), state[s*L + i] in {0,1}.
+ * Initial states: 0 = full, 1 = empty, 2 = random half (bit j of the INIT word of group g
+ * at site i is the occupation of sample 32g+j).
+ * ------------------------------------------------------------------------------------- */
+int orc_init(uint8_t *state, uint32_t L, uint32_t S, int mode, uint64_t seed)
+{
+    if (S % 32u) return 1;
+    for (uint32_t s = 0; s < S; ++s) {
+        for (uint32_t i = 0; i < L; ++i) {
+            uint8_t v;
+            if (mode == 0) v = 1;
+            else if (mode == 1) v = 0;
+            else if (mode == 2) {
+                uint32_t out[4];
+                orc_block(seed, i, 0u, s / 32u, ORC_TAG_INIT << 28, out);
+                v = (uint8_t)((out[0] >> (s % 32u)) & 1u);
+            } else return 1;
+            state[(uint64_t)s * L + i] = v;
+        }
+    }
+    return 0;
+}
+
+/* ---------------------------------------------------------------------------------------
+ * One window update for one sample (Alg. 1's decision tree on the bond the orientation
+ * picks; Eq. (1) rates through R3's thresholds).  Sites a, b, c are consecutive.
+ *   o = 0: bond (a, b), fission target c   (Alg. 1 "fission high")
+ *   o = 1: bond (b, c), fission target a   (Alg. 1 "fission low")
+ * u < T_D: diffusion swaps the bond; else if both bond sites are occupied:
+ * u < T_DA annihilates them, otherwise the target becomes occupied.
+ * Returns the change in particle number (checked to be one of +1, -2, 0).
+ * ------------------------------------------------------------------------------------- */
+static int orc_window(uint8_t *sa, uint8_t *sb, uint8_t *sc, uint32_t o, uint64_t u,
+                      uint64_t t_d, uint64_t t_da)
+{
+    uint8_t *q = o ? sc : sa; /* the pair partner of b */
+    uint8_t *t = o ? sa : sc; /* the fission target    */
+    int before = *sa + *sb + *sc;
+    if (u < t_d) {
+        uint8_t tmp = *sb;
+        *sb = *q;
+        *q = tmp;
+    } else if (*sb == 1 && *q == 1) {
+        if (u < t_da) {
+            *sb = 0;
+            *q = 0;
+        } else {
+            *t = 1;
+        }
+    }
+    return *sa + *sb + *sc - before;
+}
+
+typedef struct {
+    uint32_t L, S;
+    uint64_t t_d, t_da, seed;
+    uint8_t *state;
+    uint64_t n_begin, n_end;
+    const uint64_t *rec_sub;
+    uint32_t n_rec;
+    uint64_t *rec_total;   /* [n_rec], summed over all threads under a mutex */
+    uint32_t *rec_sample;  /* [n_rec][S] or NULL */
+    uint64_t *events;      /* [3]: diffusion swaps that moved a particle, annihilations, fissions */
+    pthread_mutex_t *mu;
+    uint32_t g_begin, g_end;
+    int bad;               /* set if a window changed N by something other than +1,-2,0 */
+} orc_job;
+
+static void orc_count(orc_job *jb, uint32_t g, uint32_t r, uint64_t *tot)
+{
+    for (uint32_t j = 0; j < 32; ++j) {
+        uint32_t s = 32u * g + j;
+        uint32_t cnt = 0;
+        for (uint32_t i = 0; i < jb->L; ++i) cnt += jb->state[(uint64_t)s * jb->L + i];
+        tot[r] += cnt;
+        if (jb->rec_sample) jb->rec_sample[(uint64_t)r * jb->S + s] = cnt;
+    }
+}
+
+static void *orc_worker(void *arg)
+{
+    orc_job *jb = (orc_job *)arg;
+    const uint32_t L = jb->L, K = L / 3u;
+    uint64_t *tot = (uint64_t *)calloc(jb->n_rec ? jb->n_rec : 1, sizeof(uint64_t));
+    uint64_t ev[3] = {0, 0, 0};
+    for (uint32_t g = jb->g_begin; g < jb->g_end; ++g) {
+        const uint32_t h = (32u * g) / 128u; /* phase group: 128 samples */
+        uint32_t r = 0;
+        while (r < jb->n_rec && jb->rec_sub[r] < jb->n_begin) ++r;
+        for (uint64_t n = jb->n_begin;; ++n) {
+            /* records of the state after n sub-steps */
+            while (r < jb->n_rec && jb->rec_sub[r] == n) { orc_count(jb, g, r, tot); ++r; }
+            if (n == jb->n_end) break;
+            const uint32_t phi = orc_phase(jb->seed, L, h, (uint32_t)n);
+            for (uint32_t k = 0; k < K; ++k) {
+                /* 33 words: O and planes P31..P0 (blocks 0..8) */
+                uint32_t words[36];
+                for (uint32_t b = 0; b < 9; ++b)
+                    orc_block(jb->seed, k, (uint32_t)n, g, (ORC_TAG_DYN << 28) | b, words + 4 * b);
+                const uint32_t O = words[0];
+                /* plane P_m is words[32 - m] for m = 31..0 */
+                const uint32_t ia = (uint32_t)(((uint64_t)phi + 3ull * k) % L);
+                const uint32_t ib = (uint32_t)(((uint64_t)phi + 3ull * k + 1) % L);
+                const uint32_t ic = (uint32_t)(((uint64_t)phi + 3ull * k + 2) % L);
+                for (uint32_t j = 0; j < 32; ++j) {
+                    uint64_t u = 0;
+                    for (int m = 31; m >= 0; --m)
+                        u |= (uint64_t)((words[32 - m] >> j) & 1u) << m;
+                    const uint32_t o = (O >> j) & 1u;
+                    uint8_t *row = jb->state + (uint64_t)(32u * g + j) * L;
+                    uint8_t before_b = row[ib], before_q = o ? row[ic] : row[ia];
+                    int dn = orc_window(row + ia, row + ib, row + ic, o, u, jb->t_d, jb->t_da);
+                    if (dn != 0 && dn != 1 && dn != -2) jb->bad = 1;
+                    if (dn == -2) ev[1]++;
+                    else if (dn == 1) ev[2]++;
+                    else if (u < jb->t_d && before_b != before_q) ev[0]++;
+                }
+            }
+        }
+    }
+    pthread_mutex_lock(jb->mu);
+    for (uint32_t r = 0; r < jb->n_rec; ++r) jb->rec_total[r] += tot[r];
+    if (jb->events) for (int e = 0; e < 3; ++e) jb->events[e] += ev[e];
+    pthread_mutex_unlock(jb->mu);
+    free(tot);
+    return NULL;
+}
+
+/*
+ * Run the window schedule from the state after n_begin sub-steps to the state after n_end.
+ * rec_sub: sorted sub-step indices in [n_begin, n_end]; the state after rec_sub[r] sub-steps
+ * is counted into rec_total[r] (+= over all samples) and rec_sample[r][s] (if non-NULL).
+ * events (nullable, [3]) accumulates moving swaps, annihilations and fissions.
+ * Returns 0, or 1 on bad arguments, or 2 if the particle-number invariant failed.
+ */
+int orc_run(uint32_t L, uint32_t S, uint64_t t_d, uint64_t t_da, uint64_t seed,
+            uint8_t *state, uint64_t n_begin, uint64_t n_end, const uint64_t *rec_sub,
+            uint32_t n_rec, uint64_t *rec_total, uint32_t *rec_sample, uint64_t *events,
+            int n_threads)
+{
+    if (L < 3 || S % 32u || n_end < n_begin || n_end > 0xFFFFFFFFull) return 1;
+    const uint32_t G = S / 32u;
+    if (n_threads < 1) n_threads = 1;
+    if ((uint32_t)n_threads > G) n_threads = (int)G;
+    for (uint32_t r = 0; r < n_rec; ++r) rec_total[r] = 0;
+    if (events) events[0] = events[1] = events[2] = 0;
+    pthread_mutex_t mu = PTHREAD_MUTEX_INITIALIZER;
+    orc_job *jobs = (orc_job *)calloc((size_t)n_threads, sizeof(orc_job));
+    pthread_t *th = (pthread_t *)calloc((size_t)n_threads, sizeof(pthread_t));
+    for (int t = 0; t < n_threads; ++t) {
+        orc_job *jb = &jobs[t];
+        jb->L = L; jb->S = S; jb->t_d = t_d; jb->t_da = t_da; jb->seed = seed;
+        jb->state = state; jb->n_begin = n_begin; jb->n_end = n_end;
+        jb->rec_sub = rec_sub; jb->n_rec = n_rec; jb->rec_total = rec_total;
+        jb->rec_sample = rec_sample; jb->events = events; jb->mu = &mu;
+        jb->g_begin = (uint32_t)((uint64_t)G * t / n_threads);
+        jb->g_end = (uint32_t)((uint64_t)G * (t + 1) / n_threads);
+        pthread_create(&th[t], NULL, orc_worker, jb);
+    }
+    int bad = 0;
+    for (int t = 0; t < n_threads; ++t) {
+        pthread_join(th[t], NULL);
+        bad |= jobs[t].bad;
+    }
+    free(jobs);
+    free(th);
+    return bad ? 2 : 0;
+}
+
+/* ---------------------------------------------------------------------------------------
+ * Alg. 1, random-sequential: attempt m of sample s draws the Philox block
+ * (m lo, m hi, s, TAG_RS<<28).  Site i = floor(x0*L/2^32); diffuse iff x1 < T_D; else, on
+ * an occupied pair (i, i+1), annihilate iff x2 < T_P, else fission to i-1 iff x3 < 2^31,
+ * otherwise to i+2.  One attempt is 1/L MCS.  Records at MCS times (state after t*L
+ * attempts).  attempt_begin is the global attempt index of the first attempt.
+ * ------------------------------------------------------------------------------------- */
+typedef struct {
+    uint32_t L, S;
+    uint64_t t_d, t_p, seed;
+    uint8_t *state;
+    uint64_t a_begin, a_end;
+    const uint64_t *rec_att;
+    uint32_t n_rec;
+    uint64_t *rec_total;
+    uint32_t *rec_sample;
+    pthread_mutex_t *mu;
+    uint32_t s_begin, s_end;
+} orc_rs_job;
+
+static void *orc_rs_worker(void *arg)
+{
+    orc_rs_job *jb = (orc_rs_job *)arg;
+    const uint32_t L = jb->L;
+    uint64_t *tot = (uint64_t *)calloc(jb->n_rec ? jb->n_rec : 1, sizeof(uint64_t));
+    for (uint32_t s = jb->s_begin; s < jb->s_end; ++s) {
+        uint8_t *q = jb->state + (uint64_t)s * L;
+        uint32_t r = 0;
+        while (r < jb->n_rec && jb->rec_att[r] < jb->a_begin) ++r;
+        for (uint64_t m = jb->a_begin;; ++m) {
+            while (r < jb->n_rec && jb->rec_att[r] == m) {
+                uint32_t cnt = 0;
+                for (uint32_t i = 0; i < L; ++i) cnt += q[i];
+                tot[r] += cnt;
+                if (jb->rec_sample) jb->rec_sample[(uint64_t)r * jb->S + s] = cnt;
+                ++r;
+            }
+            if (m == jb->a_end) break;
+            uint32_t x[4];
+            orc_block(jb->seed, (uint32_t)m, (uint32_t)(m >> 32), s, ORC_TAG_RS << 28, x);
+            const uint32_t i = (uint32_t)(((uint64_t)x[0] * L) >> 32);
+            const uint32_t i1 = (i + 1u) % L;
+            if ((uint64_t)x[1] < jb->t_d) {
+                uint8_t tmp = q[i];
+                q[i] = q[i1];
+                q[i1] = tmp;
+            } else if (q[i] == 1 && q[i1] == 1) {
+                if ((uint64_t)x[2] < jb->t_p) {
+                    q[i] = 0;
+                    q[i1] = 0;
+                } else if (x[3] < 0x80000000u) {
+                    q[(i + L - 1u) % L] = 1;
+                } else {
+                    q[(i + 2u) % L] = 1;
+                }
+            }
+        }
+    }
+    pthread_mutex_lock(jb->mu);
+    for (uint32_t r = 0; r < jb->n_rec; ++r) jb->rec_total[r] += tot[r];
+    pthread_mutex_unlock(jb->mu);
+    free(tot);
+    return NULL;
+}
+
+int orc_rs_run(uint32_t L, uint32_t S, uint64_t t_d, uint64_t t_p, uint64_t seed,
+               uint8_t *state, uint64_t a_begin, uint64_t a_end, const uint64_t *rec_att,
+               uint32_t n_rec, uint64_t *rec_total, uint32_t *rec_sample, int n_threads)
+{
+    if (L < 3 || S == 0 || a_end < a_begin) return 1;
+    if (n_threads < 1) n_threads = 1;
+    if ((uint32_t)n_threads > S) n_threads = (int)S;
+    for (uint32_t r = 0; r < n_rec; ++r) rec_total[r] = 0;
+    pthread_mutex_t mu = PTHREAD_MUTEX_INITIALIZER;
+    orc_rs_job *jobs = (orc_rs_job *)calloc((size_t)n_threads, sizeof(orc_rs_job));
+    pthread_t *th = (pthread_t *)calloc((size_t)n_threads, sizeof(pthread_t));
+    for (int t = 0; t < n_threads; ++t) {
+        orc_rs_job *jb = &jobs[t];
+        jb->L = L; jb->S = S; jb->t_d = t_d; jb->t_p = t_p; jb->seed = seed;
+        jb->state = state; jb->a_begin = a_begin; jb->a_end = a_end;
+        jb->rec_att = rec_att; jb->n_rec = n_rec; jb->rec_total = rec_total;
+        jb->rec_sample = rec_sample; jb->mu = &mu;
+        jb->s_begin = (uint32_t)((uint64_t)S * t / n_threads);
+        jb->s_end = (uint32_t)((uint64_t)S * (t + 1) / n_threads);
+        pthread_create(&th[t], NULL, orc_rs_worker, jb);
+    }
+    for (int t = 0; t < n_threads; ++t) pthread_join(th[t], NULL);
+    free(jobs);
+    free(th);
+    return 0;
+}
+
+/* Canonical packing: word [g][i] bit j <-> state[(32g+j)*L + i]. */
+void orc_pack(const uint8_t *state, uint32_t L, uint32_t S, uint32_t *words)
+{
+    for (uint32_t g = 0; g < S / 32u; ++g)
+        for (uint32_t i = 0; i < L; ++i) {
+            uint32_t w = 0;
+            for (uint32_t j = 0; j < 32; ++j)
+                w |= (uint32_t)(state[(uint64_t)(32u * g + j) * L + i] & 1u) << j;
+            words[(uint64_t)g * L + i] = w;
+        }
+}
+
+void orc_unpack(const uint32_t *words, uint32_t L, uint32_t S, uint8_t *state)
+{
+    for (uint32_t g = 0; g < S / 32u; ++g)
+        for (uint32_t i = 0; i < L; ++i)
+            for (uint32_t j = 0; j < 32; ++j)
+                state[(uint64_t)(32u * g + j) * L + i] =
+                    (uint8_t)((words[(uint64_t)g * L + i] >> j) & 1u);
+}
