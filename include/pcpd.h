@@ -1,0 +1,153 @@
+/*
+ * pcpd.h -- C ABI of libpcpd.so: the bit-sliced Monte Carlo sweep of the 1+1-d pair contact
+ * process with diffusion (PCPD) on an NVIDIA GB300 (sm_103a).
+ *
+ * The method is the one of Schram, "Reaction-diffusion model Monte Carlo simulations on the
+ * GPU" (arXiv 1301.6082): reactions AA0/0AA -> AAA at rate (1-p)(1-d)/2 each, AA -> 00 at
+ * rate p(1-d), A0 <-> 0A at rate d on a periodic lattice (Sec. 2, Eq. (1)), with the bond
+ * decision tree of Alg. 1, evaluated branch-free on multispin words (Sec. 4, Alg. 2), and the
+ * density rho(t) recorded at chosen times (Sec. 5.3).  This library fixes a parallel update
+ * schedule: at every sub-step a random phase phi tiles the ring with K = floor(L/3)
+ * non-overlapping 3-site windows, each making one bond attempt per sample; MCS time t is
+ * reached after ceil(t*L/K) sub-steps (1 MCS = L attempts per sample).
+ *
+ * Samples are bit-sliced: one independent sample per bit, 32 samples per "group".
+ * Canonical lattice layout (every host or device buffer that holds a lattice):
+ *     uint32_t words[G][L], G = samples/32; bit j of words[g][i] = occupation of sample
+ *     32*g + j at site i.
+ * Random numbers: Philox4x32-10 keyed by the seed and counted by (window, sub-step, group,
+ * tag|block), so results do not depend on how the work is split or batched.
+ *
+ * Conventions for every function returning int: 0 (PCPD_OK) on success, else one of the
+ * PCPD_E* codes, with a message available from pcpd_last_error() (thread-local).  No
+ * function keeps a pointer it was passed beyond the call unless stated.  Handles are not
+ * thread-safe; distinct handles may be used from distinct threads.  Nothing in this library
+ * falls back to the CPU: without a usable CUDA device every entry that computes fails with
+ * PCPD_ENODEV.
+ */
+#ifndef PCPD_H
+#define PCPD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    PCPD_OK = 0,
+    PCPD_EINVAL = 1,   /* bad argument (range, order, NULL, size) */
+    PCPD_ENOMEM = 2,   /* a device or host allocation failed */
+    PCPD_ECUDA = 3,    /* a CUDA call failed; the message names it */
+    PCPD_ETIMEOUT = 4, /* a device-side wait ran out of its iteration budget */
+    PCPD_ESTATE = 5,   /* call out of order (e.g. record time already passed) */
+    PCPD_ENODEV = 6    /* no usable sm_100-family CUDA device */
+};
+
+enum { PCPD_INIT_FULL = 0, PCPD_INIT_EMPTY = 1, PCPD_INIT_HALF = 2 };
+
+typedef struct pcpd pcpd_t;
+
+/* Creation parameters.  Zero-initialise and set what you need. */
+typedef struct pcpd_params {
+    uint32_t L;          /* lattice sites, 3 <= L < 2^30 */
+    uint32_t samples;    /* independent samples, a positive multiple of 32, <= 2^22 */
+    double p;            /* annihilation parameter of Eq. (1), in [0, 1] */
+    double d;            /* diffusion parameter of Eq. (1), in [0, 1] */
+    uint64_t seed;       /* Philox key */
+    int init;            /* PCPD_INIT_FULL (default 0), PCPD_INIT_EMPTY or PCPD_INIT_HALF */
+    void *stream;        /* cudaStream_t for all device work; NULL = a stream owned by the handle */
+    void *dev_lattice;   /* optional caller-owned device buffer of >= 2*G*L*4 bytes, 256-byte
+                            aligned, used for the lattice and its second buffer; NULL = the
+                            handle allocates (and frees) its own */
+    size_t dev_bytes;    /* size of dev_lattice in bytes (ignored when dev_lattice is NULL) */
+    int per_sample;      /* non-zero: also keep per-sample counts at every record */
+    /* plan override, 0 = automatic.  No plan changes a result bit. */
+    uint32_t plan_threads;   /* threads per CTA (multiple of 32, <= 1024) */
+    uint32_t plan_seg_sites; /* core sites per tile for lattices that do not fit one CTA */
+    uint32_t plan_tau;       /* sub-steps per tile residency (temporal block) */
+} pcpd_params;
+
+/* Create a simulation of `samples` PCPD samples on a ring of L sites, initialised fully
+ * occupied, using the handle's own stream and memory.  Returns NULL on error (see
+ * pcpd_last_error()).  Initial state: Sec. 2's decay runs start fully occupied. */
+pcpd_t *pcpd_create(uint32_t L, uint32_t samples, double p, double d, uint64_t seed);
+
+/* Create from parameters.  On success *out receives the handle.  The lattice is initialised
+ * (full, empty, or i.i.d. Bernoulli(1/2) bits from the seed) on the handle's stream. */
+int pcpd_create_ex(const pcpd_params *prm, pcpd_t **out);
+
+/* Advance every sample by steps_mcs Monte Carlo steps (t_now -> t_now + steps_mcs) and
+ * record the occupation at each MCS time in record_times_mcs[0..n_times): strictly
+ * increasing, each in (t_now, t_now + steps_mcs]; a time equal to t_now is allowed only as
+ * the first entry and records the current state.  Work is enqueued on the handle's stream;
+ * the call returns without waiting for it.  n_times may be 0 (record_times_mcs may then be
+ * NULL).  Errors: PCPD_EINVAL (times out of order or range, sub-step count >= 2^32),
+ * PCPD_ECUDA. */
+int pcpd_run(pcpd_t *h, uint64_t steps_mcs, const uint64_t *record_times_mcs, size_t n_times);
+
+/* Number of records taken so far (all pcpd_run calls). */
+size_t pcpd_num_records(const pcpd_t *h);
+
+/* Copy the first n_times records (waits for the handle's stream): rho_out[r] =
+ * counts[r] / (L * samples) (nullable), counts_out[r] = occupied (site, sample) pairs (nullable),
+ * times_out[r] = the record's MCS time (nullable).  PCPD_EINVAL if n_times exceeds
+ * pcpd_num_records(). */
+int pcpd_density(const pcpd_t *h, double *rho_out, uint64_t *counts_out, size_t n_times);
+int pcpd_record_times(const pcpd_t *h, uint64_t *times_out, size_t n_times);
+
+/* Per-sample counts of record r into out[samples] (uint32, sample order 0..samples-1).
+ * Needs per_sample at creation; else PCPD_ESTATE. */
+int pcpd_sample_counts(const pcpd_t *h, size_t r, uint32_t *out);
+
+/* Copy the current lattice to host memory in the canonical layout (G*L words).  Waits. */
+int pcpd_get_lattice(const pcpd_t *h, uint32_t *host_out);
+
+/* Replace the lattice by host_in (canonical layout) and set the clock to `substep` completed
+ * sub-steps (MCS time = the largest t with ceil(t*L/K) <= substep).  Records are cleared.
+ * Resuming from a saved (lattice, sub-step) pair reproduces the uninterrupted run exactly. */
+int pcpd_set_lattice(pcpd_t *h, const uint32_t *host_in, uint64_t substep);
+
+/* Advance by exactly n_substeps sub-steps with no records (splice tests, fine control). */
+int pcpd_run_substeps(pcpd_t *h, uint64_t n_substeps);
+
+/* Current clock: completed sub-steps and MCS time. */
+uint64_t pcpd_substep(const pcpd_t *h);
+uint64_t pcpd_time_mcs(const pcpd_t *h);
+
+/* Block until all work enqueued for the handle has finished. */
+int pcpd_sync(pcpd_t *h);
+
+/* Release everything the handle owns.  NULL-safe. */
+void pcpd_destroy(pcpd_t *h);
+
+/* Message for the last error on this thread ("" if none). */
+const char *pcpd_last_error(void);
+
+/* Integer thresholds of the rates of Eq. (1): T_D = min(2^32, floor(d*2^32)),
+ * T_DA = min(2^32, T_D + floor(p*(1-d)*2^32)), IEEE double, no contraction.  A sample with
+ * draw u diffuses if u < T_D, else annihilates an occupied bond if u < T_DA, else fissions. */
+int pcpd_thresholds(double p, double d, uint64_t *t_d, uint64_t *t_da);
+
+/* Sub-step at which MCS time t is reached on a ring of L sites: ceil(t*L/floor(L/3)). */
+uint64_t pcpd_substep_of_time(uint32_t L, uint64_t t);
+
+/* ---- device-level entry points used by the tests (all pointers are device pointers,
+ * stream may be NULL for the default stream; the call waits for completion) ---- */
+
+/* Philox4x32-10 (Salmon et al., SC'11) on n counters ctr[n][4] under key = seed -> out[n][4]. */
+int pcpd_dev_philox(const uint32_t *ctr, uint64_t seed, uint32_t *out, size_t n, void *stream);
+
+/* The bit-plane threshold compare (the exact form of the dyadic masks of Sec. 4.2-4.3): for
+ * each of n items, words[n][33] = (O, P31, ..., P0); lane j's draw is
+ * u_j = sum_m bit_j(P_m) 2^m.  Writes masks[n][3] = (D: u < T_D, A: T_D <= u < T_DA, O),
+ * using the early-exit MSB-first compare of the sweep kernels. */
+int pcpd_dev_rate_masks(const uint32_t *words, uint64_t t_d, uint64_t t_da, uint32_t *masks,
+                        size_t n, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PCPD_H */

@@ -51,10 +51,10 @@ def lib():
             L.orc_substep_of_time.restype = C.c_uint64
             L.orc_phase.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32]
             L.orc_phase.restype = C.c_uint32
-            L.orc_init.argtypes = [u8p, C.c_uint32, C.c_uint32, C.c_int, C.c_uint64]
+            L.orc_init.argtypes = [u8p, C.c_uint32, C.c_uint32, C.c_int, C.c_uint64, C.c_uint32]
             L.orc_init.restype = C.c_int
             L.orc_run.argtypes = [C.c_uint32, C.c_uint32, C.c_uint64, C.c_uint64, C.c_uint64, u8p,
-                                  C.c_uint64, C.c_uint64, u64p, C.c_uint32, u64p, u32p, u64p, C.c_int]
+                                  C.c_uint64, C.c_uint64, u64p, C.c_uint32, u64p, u32p, u64p, C.c_int, C.c_uint32]
             L.orc_run.restype = C.c_int
             L.orc_rs_run.argtypes = [C.c_uint32, C.c_uint32, C.c_uint64, C.c_uint64, C.c_uint64, u8p,
                                      C.c_uint64, C.c_uint64, u64p, C.c_uint32, u64p, u32p, C.c_int]
@@ -93,9 +93,10 @@ def phase(seed: int, L: int, h: int, n: int) -> int:
     return int(lib().orc_phase(seed, L, h, n))
 
 
-def init_state(L: int, S: int, mode: int = MODE_FULL, seed: int = 1) -> np.ndarray:
+def init_state(L: int, S: int, mode: int = MODE_FULL, seed: int = 1, group0: int = 0) -> np.ndarray:
+    """Initial byte state [S][L] of groups group0 .. group0 + S/32 - 1 of an instance."""
     st = np.zeros((S, L), dtype=np.uint8)
-    if lib().orc_init(_p(st, C.c_uint8), L, S, mode, seed) != 0:
+    if lib().orc_init(_p(st, C.c_uint8), L, S, mode, seed, group0) != 0:
         raise ValueError("bad init arguments")
     return st
 
@@ -118,9 +119,10 @@ def unpack(words: np.ndarray) -> np.ndarray:
 
 
 def run(state: np.ndarray, p: float, d: float, seed: int, n_begin: int, n_end: int,
-        rec_sub=(), per_sample: bool = False, threads: int | None = None):
-    """Advance ``state`` (modified in place, [S][L] bytes) from sub-step n_begin to n_end on
-    the window schedule.  Returns (totals u64[R], per-sample u32[R][S] or None, events[3])."""
+        rec_sub=(), per_sample: bool = False, threads: int | None = None, group0: int = 0):
+    """Advance ``state`` (modified in place, [S][L] bytes: groups group0, group0+1, ... of an
+    instance) from sub-step n_begin to n_end on the window schedule.
+    Returns (totals u64[R], per-sample u32[R][S] or None, events[3])."""
     assert state.dtype == np.uint8 and state.flags.c_contiguous
     S, L = state.shape
     td, tda, _ = thresholds(p, d)
@@ -131,7 +133,7 @@ def run(state: np.ndarray, p: float, d: float, seed: int, n_begin: int, n_end: i
     nt = threads if threads is not None else (os.cpu_count() or 1)
     rc = lib().orc_run(L, S, td, tda, C.c_uint64(seed), _p(state, C.c_uint8), n_begin, n_end,
                        _p(rec, C.c_uint64), len(rec), _p(tot, C.c_uint64),
-                       _p(ps, C.c_uint32) if ps is not None else None, _p(ev, C.c_uint64), nt)
+                       _p(ps, C.c_uint32) if ps is not None else None, _p(ev, C.c_uint64), nt, group0)
     if rc == 2:
         raise AssertionError("oracle: a window changed the particle number by other than +1, -2, 0")
     if rc != 0:

@@ -123,9 +123,9 @@ uint32_t orc_phase(uint64_t seed, uint32_t L, uint32_t h, uint32_t n)
 /* ---------------------------------------------------------------------------------------
  * Lattice state of the oracle: one byte per (sample, site), state[s*L + i] in {0,1}.
  * Initial states: 0 = full, 1 = empty, 2 = random half (bit j of the INIT word of group g
- * at site i is the occupation of sample 32g+j).
+ * at site i is the occupation of sample 32g+j).  The state holds groups g0, g0+1, ...
  * ------------------------------------------------------------------------------------- */
-int orc_init(uint8_t *state, uint32_t L, uint32_t S, int mode, uint64_t seed)
+int orc_init(uint8_t *state, uint32_t L, uint32_t S, int mode, uint64_t seed, uint32_t g0)
 {
     if (S % 32u) return 1;
     for (uint32_t s = 0; s < S; ++s) {
@@ -135,7 +135,7 @@ int orc_init(uint8_t *state, uint32_t L, uint32_t S, int mode, uint64_t seed)
             else if (mode == 1) v = 0;
             else if (mode == 2) {
                 uint32_t out[4];
-                orc_block(seed, i, 0u, s / 32u, ORC_TAG_INIT << 28, out);
+                orc_block(seed, i, 0u, g0 + s / 32u, ORC_TAG_INIT << 28, out);
                 v = (uint8_t)((out[0] >> (s % 32u)) & 1u);
             } else return 1;
             state[(uint64_t)s * L + i] = v;
@@ -186,6 +186,7 @@ typedef struct {
     uint64_t *events;      /* [3]: diffusion swaps that moved a particle, annihilations, fissions */
     pthread_mutex_t *mu;
     uint32_t g_begin, g_end;
+    uint32_t g0;           /* group index of the state's first group (keys and phase groups) */
     int bad;               /* set if a window changed N by something other than +1,-2,0 */
 } orc_job;
 
@@ -207,7 +208,8 @@ static void *orc_worker(void *arg)
     uint64_t *tot = (uint64_t *)calloc(jb->n_rec ? jb->n_rec : 1, sizeof(uint64_t));
     uint64_t ev[3] = {0, 0, 0};
     for (uint32_t g = jb->g_begin; g < jb->g_end; ++g) {
-        const uint32_t h = (32u * g) / 128u; /* phase group: 128 samples */
+        const uint32_t gk = jb->g0 + g;        /* the group's index in the full instance */
+        const uint32_t h = (32u * gk) / 128u;  /* phase group: 128 samples */
         uint32_t r = 0;
         while (r < jb->n_rec && jb->rec_sub[r] < jb->n_begin) ++r;
         for (uint64_t n = jb->n_begin;; ++n) {
@@ -219,7 +221,7 @@ static void *orc_worker(void *arg)
                 /* 33 words: O and planes P31..P0 (blocks 0..8) */
                 uint32_t words[36];
                 for (uint32_t b = 0; b < 9; ++b)
-                    orc_block(jb->seed, k, (uint32_t)n, g, (ORC_TAG_DYN << 28) | b, words + 4 * b);
+                    orc_block(jb->seed, k, (uint32_t)n, gk, (ORC_TAG_DYN << 28) | b, words + 4 * b);
                 const uint32_t O = words[0];
                 /* plane P_m is words[32 - m] for m = 31..0 */
                 const uint32_t ia = (uint32_t)(((uint64_t)phi + 3ull * k) % L);
@@ -251,6 +253,7 @@ static void *orc_worker(void *arg)
 
 /*
  * Run the window schedule from the state after n_begin sub-steps to the state after n_end.
+ * The state holds the S/32 groups g0, g0+1, ... of an instance (g0 = 0 for all of it).
  * rec_sub: sorted sub-step indices in [n_begin, n_end]; the state after rec_sub[r] sub-steps
  * is counted into rec_total[r] (+= over all samples) and rec_sample[r][s] (if non-NULL).
  * events (nullable, [3]) accumulates moving swaps, annihilations and fissions.
@@ -259,7 +262,7 @@ static void *orc_worker(void *arg)
 int orc_run(uint32_t L, uint32_t S, uint64_t t_d, uint64_t t_da, uint64_t seed,
             uint8_t *state, uint64_t n_begin, uint64_t n_end, const uint64_t *rec_sub,
             uint32_t n_rec, uint64_t *rec_total, uint32_t *rec_sample, uint64_t *events,
-            int n_threads)
+            int n_threads, uint32_t g0)
 {
     if (L < 3 || S % 32u || n_end < n_begin || n_end > 0xFFFFFFFFull) return 1;
     const uint32_t G = S / 32u;
@@ -278,6 +281,7 @@ int orc_run(uint32_t L, uint32_t S, uint64_t t_d, uint64_t t_da, uint64_t seed,
         jb->rec_sample = rec_sample; jb->events = events; jb->mu = &mu;
         jb->g_begin = (uint32_t)((uint64_t)G * t / n_threads);
         jb->g_end = (uint32_t)((uint64_t)G * (t + 1) / n_threads);
+        jb->g0 = g0;
         pthread_create(&th[t], NULL, orc_worker, jb);
     }
     int bad = 0;

@@ -1,0 +1,514 @@
+// pcpd_capi.cu -- the C ABI of libpcpd.so (declared in include/pcpd.h): handles, thresholds,
+// time bookkeeping, tile plans and kernel launches for the bit-sliced PCPD sweep.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/pcpd.h"
+#include "pcpd_kernels.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CU(call)                                                                           \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return fail(e_ == cudaErrorMemoryAllocation ? PCPD_ENOMEM : PCPD_ECUDA, "%s: %s (%s:%d)", \
+                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                      \
+  } while (0)
+
+constexpr uint64_t kTwo32 = 4294967296ull;
+
+// Rates of Eq. (1) as integer thresholds, evaluated in double exactly as written (the
+// library is compiled with -ffp-contract=off, so no product is fused).
+uint64_t floor_scaled(double x) {
+  const double f = std::floor(x);
+  if (f <= 0.0) return 0;
+  if (f >= 4294967296.0) return kTwo32;
+  return (uint64_t)f;
+}
+
+int thresholds(double p, double d, uint64_t *td, uint64_t *tda) {
+  if (!(p >= 0.0 && p <= 1.0 && d >= 0.0 && d <= 1.0))
+    return fail(PCPD_EINVAL, "p and d must lie in [0, 1] (p=%g, d=%g)", p, d);
+  const uint64_t t_d = floor_scaled(d * 4294967296.0);
+  double a = p * (1.0 - d);
+  a = a * 4294967296.0;
+  uint64_t t_da = t_d + floor_scaled(a);
+  if (t_da > kTwo32) t_da = kTwo32;
+  *td = t_d;
+  *tda = t_da;
+  return PCPD_OK;
+}
+
+// ceil(t*L/K), K = floor(L/3): the sub-step at which MCS time t is reached.
+uint64_t substep_of_time(uint32_t L, uint64_t t) {
+  const unsigned __int128 K = L / 3u;
+  const unsigned __int128 num = (unsigned __int128)t * L;
+  return (uint64_t)((num + K - 1) / K);
+}
+
+// Largest MCS time reached after n sub-steps: floor(n*K/L).
+uint64_t time_of_substep(uint32_t L, uint64_t n) {
+  return (uint64_t)(((unsigned __int128)n * (L / 3u)) / L);
+}
+
+pcpdk::Thresholds split_thresholds(uint64_t td, uint64_t tda) {
+  pcpdk::Thresholds T;
+  T.td_full = td >= kTwo32;
+  T.tda_full = tda >= kTwo32;
+  T.td = (uint32_t)(T.td_full ? 0u : td);
+  T.tda = (uint32_t)(T.tda_full ? 0u : tda);
+  return T;
+}
+
+int device_check() {
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess || n == 0)
+    return fail(PCPD_ENODEV, "no CUDA device (%s)", e == cudaSuccess ? "count 0" : cudaGetErrorString(e));
+  int dev = 0, major = 0;
+  CU(cudaGetDevice(&dev));
+  CU(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev));
+  if (major != 10) return fail(PCPD_ENODEV, "device %d has compute capability %d.x; this build targets sm_103a", dev, major);
+  return PCPD_OK;
+}
+
+int smem_optin(int *bytes) {
+  int dev = 0;
+  CU(cudaGetDevice(&dev));
+  CU(cudaDeviceGetAttribute(bytes, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  return PCPD_OK;
+}
+
+// Static shared memory of the tile kernel (phase buffer + reduction slots), with margin.
+constexpr size_t kStaticSmem = sizeof(uint32_t) * pcpdk::kPhiChunk + 33 * sizeof(unsigned int) + 256;
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+struct pcpd {
+  uint32_t L = 0, K = 0, S = 0, G = 0;
+  double p = 0, d = 0;
+  uint64_t seed = 0, td = 0, tda = 0;
+  pcpdk::Thresholds T{};
+  uint32_t k0 = 0, k1 = 0;
+  int init = 0;
+  bool per_sample = false;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  uint32_t *buf[2] = {nullptr, nullptr};
+  int cur = 0;
+  bool own_mem = false;
+  uint64_t n_now = 0, t_now = 0;
+  // records
+  std::vector<uint64_t> rec_times;
+  unsigned long long *d_rec_total = nullptr;
+  uint32_t *d_rec_sample = nullptr;
+  size_t rec_cap = 0;
+  uint32_t *d_rec_sub = nullptr;
+  size_t rec_sub_cap = 0;
+  // plan
+  bool ring = true;
+  uint32_t threads = 0, core = 0, halo = 0, tau = 0, n_seg = 1;
+  size_t dyn_smem = 0;
+};
+
+namespace {
+
+int make_plan(pcpd_t *h, const pcpd_params *prm) {
+  int optin = 0;
+  int rc = smem_optin(&optin);
+  if (rc) return rc;
+  const size_t avail_words = ((size_t)optin - kStaticSmem) / 4;
+  const uint32_t L = h->L;
+  const uint32_t seg_override = prm ? prm->plan_seg_sites : 0;
+  if (seg_override == 0 && L <= avail_words) {
+    h->ring = true;
+    h->core = L;
+    h->halo = 0;
+    h->n_seg = 1;
+    h->dyn_smem = (size_t)L * 4;
+    uint32_t want = (h->K + 31u) / 32u * 32u;
+    if (want > 1024u) want = 1024u;
+    if (want < 32u) want = 32u;
+    h->threads = want;
+  } else {
+    h->ring = false;
+    h->tau = (prm && prm->plan_tau) ? prm->plan_tau : 128u;
+    h->halo = 2u * h->tau;
+    uint32_t core;
+    if (seg_override) {
+      core = seg_override;
+    } else {
+      const size_t max_core = avail_words > 2u * h->halo ? avail_words - 2u * h->halo : 0;
+      if (max_core < 1024) return fail(PCPD_EINVAL, "temporal block tau=%u too large for shared memory", h->tau);
+      const uint32_t nseg = (uint32_t)((L + max_core - 1) / max_core);
+      core = (L + nseg - 1) / nseg;
+    }
+    h->core = core;
+    h->n_seg = (L + core - 1) / core;
+    const size_t tile = (size_t)core + 2u * h->halo;
+    if (tile > avail_words) return fail(PCPD_EINVAL, "tile of %zu sites exceeds shared memory", tile);
+    if (h->n_seg < 2 || tile + 12 > L)
+      return fail(PCPD_EINVAL, "segmented plan needs >= 2 tiles each shorter than L-12 (L=%u, core=%u, halo=%u)", L, core, h->halo);
+    h->dyn_smem = tile * 4;
+    h->threads = 1024;
+  }
+  if (prm && prm->plan_threads) {
+    if (prm->plan_threads % 32 || prm->plan_threads > 1024)
+      return fail(PCPD_EINVAL, "plan_threads must be a multiple of 32 and <= 1024");
+    h->threads = prm->plan_threads;
+  }
+  return PCPD_OK;
+}
+
+int ensure_records(pcpd_t *h, size_t need) {
+  if (need <= h->rec_cap) return PCPD_OK;
+  size_t cap = h->rec_cap ? h->rec_cap : 64;
+  while (cap < need) cap *= 2;
+  unsigned long long *nt = nullptr;
+  uint32_t *ns = nullptr;
+  CU(cudaMalloc(&nt, cap * sizeof(unsigned long long)));
+  CU(cudaMemsetAsync(nt, 0, cap * sizeof(unsigned long long), h->stream));
+  if (h->per_sample) {
+    CU(cudaMalloc(&ns, cap * (size_t)h->S * sizeof(uint32_t)));
+    CU(cudaMemsetAsync(ns, 0, cap * (size_t)h->S * sizeof(uint32_t), h->stream));
+  }
+  const size_t have = h->rec_times.size();
+  if (have) {
+    CU(cudaMemcpyAsync(nt, h->d_rec_total, have * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, h->stream));
+    if (h->per_sample)
+      CU(cudaMemcpyAsync(ns, h->d_rec_sample, have * (size_t)h->S * sizeof(uint32_t), cudaMemcpyDeviceToDevice, h->stream));
+  }
+  CU(cudaStreamSynchronize(h->stream));
+  cudaFree(h->d_rec_total);
+  cudaFree(h->d_rec_sample);
+  h->d_rec_total = nt;
+  h->d_rec_sample = ns;
+  h->rec_cap = cap;
+  return PCPD_OK;
+}
+
+int ensure_rec_sub(pcpd_t *h, size_t need) {
+  if (need <= h->rec_sub_cap) return PCPD_OK;
+  size_t cap = h->rec_sub_cap ? h->rec_sub_cap : 64;
+  while (cap < need) cap *= 2;
+  CU(cudaStreamSynchronize(h->stream));
+  cudaFree(h->d_rec_sub);
+  h->d_rec_sub = nullptr;
+  CU(cudaMalloc(&h->d_rec_sub, cap * sizeof(uint32_t)));
+  h->rec_sub_cap = cap;
+  return PCPD_OK;
+}
+
+// Launch the sweep from n_now to n_end; records rec_sub[0..n) (absolute sub-steps in
+// (n_now, n_end], device copy at d_sub) go to record slots [slot0, slot0+n).
+int launch_sweep(pcpd_t *h, uint64_t n_end, const std::vector<uint64_t> &subs, size_t slot0) {
+  pcpdk::SweepParams P{};
+  P.L = h->L;
+  P.K = h->K;
+  P.G = h->G;
+  P.S = h->S;
+  P.k0 = h->k0;
+  P.k1 = h->k1;
+  P.T = h->T;
+  P.core = h->core;
+  P.halo = h->halo;
+  const dim3 block(h->threads);
+  const dim3 grid(h->n_seg, h->G);
+  size_t ri = 0;
+  if (h->ring) {
+    CU(cudaFuncSetAttribute(pcpdk::k_sweep_tile<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->dyn_smem));
+  } else {
+    CU(cudaFuncSetAttribute(pcpdk::k_sweep_tile<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->dyn_smem));
+  }
+  // RING: the whole range in launches of at most 2^20 sub-steps; SEGMENT: tau sub-steps each
+  const uint64_t chunk = h->ring ? (1ull << 20) : h->tau;
+  uint64_t n = h->n_now;
+  while (n < n_end) {
+    const uint64_t nb = (n_end - n > chunk) ? n + chunk : n_end;
+    size_t rj = ri;
+    while (rj < subs.size() && subs[rj] <= nb) ++rj;
+    P.n_begin = (uint32_t)n;
+    P.n_end = (uint32_t)nb;
+    P.rec_sub = h->d_rec_sub + ri;
+    P.n_rec = (uint32_t)(rj - ri);
+    P.rec_total = h->d_rec_total ? h->d_rec_total + slot0 + ri : nullptr;
+    P.rec_sample = h->per_sample ? h->d_rec_sample + (slot0 + ri) * (size_t)h->S : nullptr;
+    if (h->ring) {
+      P.src = h->buf[h->cur];
+      P.dst = h->buf[h->cur];
+      pcpdk::k_sweep_tile<true><<<grid, block, h->dyn_smem, h->stream>>>(P);
+    } else {
+      P.src = h->buf[h->cur];
+      P.dst = h->buf[1 - h->cur];
+      pcpdk::k_sweep_tile<false><<<grid, block, h->dyn_smem, h->stream>>>(P);
+      h->cur = 1 - h->cur;
+    }
+    CU(cudaGetLastError());
+    ri = rj;
+    n = nb;
+  }
+  h->n_now = n_end;
+  return PCPD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *pcpd_last_error(void) { return g_err.c_str(); }
+
+int pcpd_thresholds(double p, double d, uint64_t *t_d, uint64_t *t_da) {
+  if (!t_d || !t_da) return fail(PCPD_EINVAL, "NULL output");
+  return thresholds(p, d, t_d, t_da);
+}
+
+uint64_t pcpd_substep_of_time(uint32_t L, uint64_t t) { return L < 3 ? 0 : substep_of_time(L, t); }
+
+int pcpd_create_ex(const pcpd_params *prm, pcpd_t **out) {
+  if (!prm || !out) return fail(PCPD_EINVAL, "NULL argument");
+  *out = nullptr;
+  if (prm->L < 3 || prm->L >= (1u << 30)) return fail(PCPD_EINVAL, "L must satisfy 3 <= L < 2^30 (L=%u)", prm->L);
+  if (prm->samples == 0 || prm->samples % 32 || prm->samples > (1u << 22))
+    return fail(PCPD_EINVAL, "samples must be a positive multiple of 32, at most 2^22 (samples=%u)", prm->samples);
+  if (prm->init < 0 || prm->init > 2) return fail(PCPD_EINVAL, "unknown init mode %d", prm->init);
+  uint64_t td, tda;
+  int rc = thresholds(prm->p, prm->d, &td, &tda);
+  if (rc) return rc;
+  rc = device_check();
+  if (rc) return rc;
+
+  pcpd_t *h = new pcpd();
+  h->L = prm->L;
+  h->K = prm->L / 3u;
+  h->S = prm->samples;
+  h->G = prm->samples / 32u;
+  h->p = prm->p;
+  h->d = prm->d;
+  h->seed = prm->seed;
+  h->td = td;
+  h->tda = tda;
+  h->T = split_thresholds(td, tda);
+  h->k0 = (uint32_t)(prm->seed & 0xFFFFFFFFu);
+  h->k1 = (uint32_t)(prm->seed >> 32);
+  h->init = prm->init;
+  h->per_sample = prm->per_sample != 0;
+  auto bail = [&](int code) {
+    pcpd_destroy(h);
+    return code;
+  };
+  rc = make_plan(h, prm);
+  if (rc) return bail(rc);
+  if (prm->stream) {
+    h->stream = (cudaStream_t)prm->stream;
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(fail(PCPD_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e)));
+    h->own_stream = true;
+  }
+  const size_t words = (size_t)h->G * h->L;
+  if (prm->dev_lattice) {
+    if (prm->dev_bytes < 2 * words * 4 || ((uintptr_t)prm->dev_lattice & 255u))
+      return bail(fail(PCPD_EINVAL, "dev_lattice must be 256-byte aligned and hold 2*G*L words (%zu bytes)", 2 * words * 4));
+    h->buf[0] = (uint32_t *)prm->dev_lattice;
+    h->buf[1] = h->buf[0] + words;
+  } else {
+    cudaError_t e = cudaMalloc(&h->buf[0], 2 * words * 4);
+    if (e != cudaSuccess) return bail(fail(PCPD_ENOMEM, "cudaMalloc(%zu): %s", 2 * words * 4, cudaGetErrorString(e)));
+    h->buf[1] = h->buf[0] + words;
+    h->own_mem = true;
+  }
+  pcpdk::k_init<<<1024, 256, 0, h->stream>>>(h->buf[0], h->L, h->G, h->init, h->k0, h->k1);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return bail(fail(PCPD_ECUDA, "init launch: %s", cudaGetErrorString(e)));
+  *out = h;
+  return PCPD_OK;
+}
+
+pcpd_t *pcpd_create(uint32_t L, uint32_t samples, double p, double d, uint64_t seed) {
+  pcpd_params prm;
+  memset(&prm, 0, sizeof prm);
+  prm.L = L;
+  prm.samples = samples;
+  prm.p = p;
+  prm.d = d;
+  prm.seed = seed;
+  pcpd_t *h = nullptr;
+  return pcpd_create_ex(&prm, &h) == PCPD_OK ? h : nullptr;
+}
+
+void pcpd_destroy(pcpd_t *h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->own_mem) cudaFree(h->buf[0]);
+  cudaFree(h->d_rec_total);
+  cudaFree(h->d_rec_sample);
+  cudaFree(h->d_rec_sub);
+  if (h->own_stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+int pcpd_run(pcpd_t *h, uint64_t steps_mcs, const uint64_t *times, size_t n_times) {
+  if (!h) return fail(PCPD_EINVAL, "NULL handle");
+  if (n_times && !times) return fail(PCPD_EINVAL, "record_times_mcs is NULL");
+  const uint64_t t_end = h->t_now + steps_mcs;
+  if (t_end < h->t_now) return fail(PCPD_EINVAL, "time overflow");
+  const uint64_t n_end = steps_mcs ? substep_of_time(h->L, t_end) : h->n_now;
+  if (n_end > 0xFFFFFFFFull) return fail(PCPD_EINVAL, "sub-step count %llu would reach 2^32", (unsigned long long)n_end);
+  bool now_first = false;
+  std::vector<uint64_t> subs;
+  for (size_t i = 0; i < n_times; ++i) {
+    const uint64_t t = times[i];
+    if (i && t <= times[i - 1]) return fail(PCPD_EINVAL, "record times must be strictly increasing");
+    if (t == h->t_now && i == 0 && h->n_now == substep_of_time(h->L, t)) {
+      now_first = true;
+      continue;
+    }
+    if (t <= h->t_now || t > t_end)
+      return fail(PCPD_EINVAL, "record time %llu outside (%llu, %llu]", (unsigned long long)t,
+                  (unsigned long long)h->t_now, (unsigned long long)t_end);
+    subs.push_back(substep_of_time(h->L, t));
+  }
+  const size_t slot0 = h->rec_times.size();
+  int rc = ensure_records(h, slot0 + n_times);
+  if (rc) return rc;
+  size_t slot = slot0;
+  if (now_first) {
+    pcpdk::k_count<<<h->G, 256, 0, h->stream>>>(h->buf[h->cur], h->L, h->S, h->d_rec_total + slot,
+                                                 h->per_sample ? h->d_rec_sample + slot * (size_t)h->S : nullptr);
+    CU(cudaGetLastError());
+    ++slot;
+  }
+  if (!subs.empty()) {
+    rc = ensure_rec_sub(h, subs.size());
+    if (rc) return rc;
+    std::vector<uint32_t> s32(subs.begin(), subs.end());
+    CU(cudaMemcpyAsync(h->d_rec_sub, s32.data(), s32.size() * 4, cudaMemcpyHostToDevice, h->stream));
+    CU(cudaStreamSynchronize(h->stream));  // s32 is a local buffer
+  }
+  rc = launch_sweep(h, n_end, subs, slot);
+  if (rc) return rc;
+  for (size_t i = 0; i < n_times; ++i) h->rec_times.push_back(times[i]);
+  h->t_now = t_end;
+  return PCPD_OK;
+}
+
+int pcpd_run_substeps(pcpd_t *h, uint64_t n_substeps) {
+  if (!h) return fail(PCPD_EINVAL, "NULL handle");
+  const uint64_t n_end = h->n_now + n_substeps;
+  if (n_end > 0xFFFFFFFFull) return fail(PCPD_EINVAL, "sub-step count would reach 2^32");
+  std::vector<uint64_t> none;
+  int rc = launch_sweep(h, n_end, none, h->rec_times.size());
+  if (rc) return rc;
+  h->t_now = time_of_substep(h->L, h->n_now);
+  return PCPD_OK;
+}
+
+size_t pcpd_num_records(const pcpd_t *h) { return h ? h->rec_times.size() : 0; }
+
+uint64_t pcpd_substep(const pcpd_t *h) { return h ? h->n_now : 0; }
+uint64_t pcpd_time_mcs(const pcpd_t *h) { return h ? h->t_now : 0; }
+
+int pcpd_sync(pcpd_t *h) {
+  if (!h) return fail(PCPD_EINVAL, "NULL handle");
+  CU(cudaStreamSynchronize(h->stream));
+  return PCPD_OK;
+}
+
+int pcpd_density(const pcpd_t *h, double *rho_out, uint64_t *counts_out, size_t n) {
+  if (!h) return fail(PCPD_EINVAL, "NULL handle");
+  if (n > h->rec_times.size()) return fail(PCPD_EINVAL, "only %zu records", h->rec_times.size());
+  if (n == 0) return PCPD_OK;
+  std::vector<unsigned long long> c(n);
+  CU(cudaMemcpyAsync(c.data(), h->d_rec_total, n * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  const double denom = (double)h->L * (double)h->S;
+  for (size_t i = 0; i < n; ++i) {
+    if (counts_out) counts_out[i] = c[i];
+    if (rho_out) rho_out[i] = (double)c[i] / denom;
+  }
+  return PCPD_OK;
+}
+
+int pcpd_record_times(const pcpd_t *h, uint64_t *times_out, size_t n) {
+  if (!h || !times_out) return fail(PCPD_EINVAL, "NULL argument");
+  if (n > h->rec_times.size()) return fail(PCPD_EINVAL, "only %zu records", h->rec_times.size());
+  for (size_t i = 0; i < n; ++i) times_out[i] = h->rec_times[i];
+  return PCPD_OK;
+}
+
+int pcpd_sample_counts(const pcpd_t *h, size_t r, uint32_t *out) {
+  if (!h || !out) return fail(PCPD_EINVAL, "NULL argument");
+  if (!h->per_sample) return fail(PCPD_ESTATE, "per-sample counts were not requested at creation");
+  if (r >= h->rec_times.size()) return fail(PCPD_EINVAL, "record %zu does not exist", r);
+  CU(cudaMemcpyAsync(out, h->d_rec_sample + r * (size_t)h->S, (size_t)h->S * 4, cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  return PCPD_OK;
+}
+
+int pcpd_get_lattice(const pcpd_t *h, uint32_t *host_out) {
+  if (!h || !host_out) return fail(PCPD_EINVAL, "NULL argument");
+  CU(cudaMemcpyAsync(host_out, h->buf[h->cur], (size_t)h->G * h->L * 4, cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  return PCPD_OK;
+}
+
+int pcpd_set_lattice(pcpd_t *h, const uint32_t *host_in, uint64_t substep) {
+  if (!h || !host_in) return fail(PCPD_EINVAL, "NULL argument");
+  if (substep > 0xFFFFFFFFull) return fail(PCPD_EINVAL, "sub-step must be < 2^32");
+  CU(cudaMemcpyAsync(h->buf[h->cur], host_in, (size_t)h->G * h->L * 4, cudaMemcpyHostToDevice, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  h->n_now = substep;
+  h->t_now = time_of_substep(h->L, substep);
+  h->rec_times.clear();
+  if (h->d_rec_total) CU(cudaMemsetAsync(h->d_rec_total, 0, h->rec_cap * sizeof(unsigned long long), h->stream));
+  if (h->d_rec_sample) CU(cudaMemsetAsync(h->d_rec_sample, 0, h->rec_cap * (size_t)h->S * 4, h->stream));
+  return PCPD_OK;
+}
+
+int pcpd_dev_philox(const uint32_t *ctr, uint64_t seed, uint32_t *out, size_t n, void *stream) {
+  int rc = device_check();
+  if (rc) return rc;
+  if (n == 0) return PCPD_OK;
+  if (!ctr || !out) return fail(PCPD_EINVAL, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  pcpdk::k_philox<<<256, 256, 0, s>>>(ctr, (uint32_t)seed, (uint32_t)(seed >> 32), out, n);
+  CU(cudaGetLastError());
+  CU(cudaStreamSynchronize(s));
+  return PCPD_OK;
+}
+
+int pcpd_dev_rate_masks(const uint32_t *words, uint64_t t_d, uint64_t t_da, uint32_t *masks,
+                        size_t n, void *stream) {
+  int rc = device_check();
+  if (rc) return rc;
+  if (n == 0) return PCPD_OK;
+  if (!words || !masks) return fail(PCPD_EINVAL, "NULL argument");
+  if (t_d > kTwo32 || t_da > kTwo32 || t_d > t_da) return fail(PCPD_EINVAL, "need T_D <= T_DA <= 2^32");
+  cudaStream_t s = (cudaStream_t)stream;
+  pcpdk::k_rate_masks<<<256, 256, 0, s>>>(words, split_thresholds(t_d, t_da), masks, n);
+  CU(cudaGetLastError());
+  CU(cudaStreamSynchronize(s));
+  return PCPD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,207 @@
+"""Thin ctypes binding of libpcpd.so (declared in include/pcpd.h).
+
+Argument marshalling only: every step of the sweep runs in the library's CUDA kernels.
+There is no CPU fallback; if the library is missing or no CUDA device is usable, the calls
+raise.  PyTorch is optional here and only supplies device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpcpd.so")
+
+PCPD_OK, PCPD_EINVAL, PCPD_ENOMEM, PCPD_ECUDA, PCPD_ETIMEOUT, PCPD_ESTATE, PCPD_ENODEV = range(7)
+INIT_FULL, INIT_EMPTY, INIT_HALF = 0, 1, 2
+
+_u32p = C.POINTER(C.c_uint32)
+_u64p = C.POINTER(C.c_uint64)
+_f64p = C.POINTER(C.c_double)
+
+
+class PcpdError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"pcpd error {code}: {msg}")
+        self.code = code
+
+
+class Params(C.Structure):
+    _fields_ = [("L", C.c_uint32), ("samples", C.c_uint32), ("p", C.c_double), ("d", C.c_double),
+                ("seed", C.c_uint64), ("init", C.c_int), ("stream", C.c_void_p),
+                ("dev_lattice", C.c_void_p), ("dev_bytes", C.c_size_t), ("per_sample", C.c_int),
+                ("plan_threads", C.c_uint32), ("plan_seg_sites", C.c_uint32), ("plan_tau", C.c_uint32)]
+
+
+# (name, restype, argtypes) of every exported entry point in include/pcpd.h
+SIGNATURES = [
+    ("pcpd_create", C.c_void_p, [C.c_uint32, C.c_uint32, C.c_double, C.c_double, C.c_uint64]),
+    ("pcpd_create_ex", C.c_int, [C.POINTER(Params), C.POINTER(C.c_void_p)]),
+    ("pcpd_run", C.c_int, [C.c_void_p, C.c_uint64, _u64p, C.c_size_t]),
+    ("pcpd_num_records", C.c_size_t, [C.c_void_p]),
+    ("pcpd_density", C.c_int, [C.c_void_p, _f64p, _u64p, C.c_size_t]),
+    ("pcpd_record_times", C.c_int, [C.c_void_p, _u64p, C.c_size_t]),
+    ("pcpd_sample_counts", C.c_int, [C.c_void_p, C.c_size_t, _u32p]),
+    ("pcpd_get_lattice", C.c_int, [C.c_void_p, _u32p]),
+    ("pcpd_set_lattice", C.c_int, [C.c_void_p, _u32p, C.c_uint64]),
+    ("pcpd_run_substeps", C.c_int, [C.c_void_p, C.c_uint64]),
+    ("pcpd_substep", C.c_uint64, [C.c_void_p]),
+    ("pcpd_time_mcs", C.c_uint64, [C.c_void_p]),
+    ("pcpd_sync", C.c_int, [C.c_void_p]),
+    ("pcpd_destroy", None, [C.c_void_p]),
+    ("pcpd_last_error", C.c_char_p, []),
+    ("pcpd_thresholds", C.c_int, [C.c_double, C.c_double, _u64p, _u64p]),
+    ("pcpd_substep_of_time", C.c_uint64, [C.c_uint32, C.c_uint64]),
+    ("pcpd_dev_philox", C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_size_t, C.c_void_p]),
+    ("pcpd_dev_rate_masks", C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_void_p, C.c_size_t, C.c_void_p]),
+]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libpcpd.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError(f"{path} is missing: build it with paper_1301_6082_gb300.build.build()")
+        lib = C.CDLL(path)
+        for name, res, args in SIGNATURES:
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(rc: int):
+    if rc != PCPD_OK:
+        raise PcpdError(rc, load().pcpd_last_error().decode())
+
+
+def thresholds(p: float, d: float):
+    td, tda = C.c_uint64(), C.c_uint64()
+    _check(load().pcpd_thresholds(p, d, C.byref(td), C.byref(tda)))
+    return int(td.value), int(tda.value)
+
+
+def substep_of_time(L: int, t: int) -> int:
+    return int(load().pcpd_substep_of_time(L, t))
+
+
+def _ptr(a: np.ndarray, t):
+    return a.ctypes.data_as(C.POINTER(t))
+
+
+class Pcpd:
+    """One simulation handle: `samples` bit-sliced PCPD samples on a ring of L sites."""
+
+    def __init__(self, L: int, samples: int, p: float, d: float, seed: int = 1,
+                 init: int = INIT_FULL, per_sample: bool = False, stream=None,
+                 dev_lattice=None, plan_threads: int = 0, plan_seg_sites: int = 0,
+                 plan_tau: int = 0):
+        lib = load()
+        prm = Params()
+        prm.L, prm.samples, prm.p, prm.d, prm.seed, prm.init = L, samples, p, d, seed, init
+        prm.per_sample = 1 if per_sample else 0
+        prm.plan_threads, prm.plan_seg_sites, prm.plan_tau = plan_threads, plan_seg_sites, plan_tau
+        if stream is not None:
+            prm.stream = C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+        self._keep = dev_lattice
+        if dev_lattice is not None:   # a torch CUDA tensor (or any object with data_ptr/nbytes)
+            prm.dev_lattice = C.c_void_p(int(dev_lattice.data_ptr()))
+            prm.dev_bytes = int(dev_lattice.numel() * dev_lattice.element_size())
+        h = C.c_void_p()
+        _check(lib.pcpd_create_ex(C.byref(prm), C.byref(h)))
+        self._h = h
+        self.L, self.S, self.p, self.d, self.seed = L, samples, p, d, seed
+        self.G = samples // 32
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().pcpd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def run(self, steps_mcs: int, record_times=()):
+        t = np.ascontiguousarray(record_times, dtype=np.uint64)
+        _check(load().pcpd_run(self._h, steps_mcs, _ptr(t, C.c_uint64) if t.size else None, t.size))
+
+    def run_substeps(self, n: int):
+        _check(load().pcpd_run_substeps(self._h, n))
+
+    @property
+    def num_records(self) -> int:
+        return int(load().pcpd_num_records(self._h))
+
+    @property
+    def substep(self) -> int:
+        return int(load().pcpd_substep(self._h))
+
+    @property
+    def time_mcs(self) -> int:
+        return int(load().pcpd_time_mcs(self._h))
+
+    def counts(self) -> np.ndarray:
+        n = self.num_records
+        c = np.zeros(n, dtype=np.uint64)
+        if n:
+            _check(load().pcpd_density(self._h, None, _ptr(c, C.c_uint64), n))
+        return c
+
+    def density(self) -> np.ndarray:
+        n = self.num_records
+        r = np.zeros(n, dtype=np.float64)
+        if n:
+            _check(load().pcpd_density(self._h, _ptr(r, C.c_double), None, n))
+        return r
+
+    def record_times(self) -> np.ndarray:
+        n = self.num_records
+        t = np.zeros(n, dtype=np.uint64)
+        if n:
+            _check(load().pcpd_record_times(self._h, _ptr(t, C.c_uint64), n))
+        return t
+
+    def sample_counts(self, r: int) -> np.ndarray:
+        out = np.zeros(self.S, dtype=np.uint32)
+        _check(load().pcpd_sample_counts(self._h, r, _ptr(out, C.c_uint32)))
+        return out
+
+    def lattice(self) -> np.ndarray:
+        out = np.zeros((self.G, self.L), dtype=np.uint32)
+        _check(load().pcpd_get_lattice(self._h, _ptr(out, C.c_uint32)))
+        return out
+
+    def set_lattice(self, words: np.ndarray, substep: int):
+        w = np.ascontiguousarray(words, dtype=np.uint32)
+        assert w.shape == (self.G, self.L)
+        _check(load().pcpd_set_lattice(self._h, _ptr(w, C.c_uint32), substep))
+
+    def sync(self):
+        _check(load().pcpd_sync(self._h))
+
+
+def dev_philox(ctr_dev, seed: int, out_dev, n: int, stream=None):
+    """Device Philox on torch CUDA tensors ctr_dev / out_dev (uint32-compatible, [n,4])."""
+    s = C.c_void_p(int(getattr(stream, "cuda_stream", 0) or 0)) if stream is not None else None
+    _check(load().pcpd_dev_philox(C.c_void_p(ctr_dev.data_ptr()), seed, C.c_void_p(out_dev.data_ptr()), n, s))
+
+
+def dev_rate_masks(words_dev, t_d: int, t_da: int, masks_dev, n: int, stream=None):
+    s = C.c_void_p(int(getattr(stream, "cuda_stream", 0) or 0)) if stream is not None else None
+    _check(load().pcpd_dev_rate_masks(C.c_void_p(words_dev.data_ptr()), t_d, t_da,
+                                      C.c_void_p(masks_dev.data_ptr()), n, s))

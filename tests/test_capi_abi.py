@@ -1,0 +1,78 @@
+"""CPU-side checks of the boundary: the library builds for sm_103a, loads, exports every
+entry point include/pcpd.h declares, and its host-only helpers (thresholds, time) agree with
+the oracle's.  No kernel is launched here."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1301_6082_gb300 import build, pcpd
+    build.build()
+    return pcpd.load()
+
+
+def declared_functions():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"\b(pcpd_\w+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_header():
+    from paper_1301_6082_gb300 import pcpd
+    bound = {n for n, _, _ in pcpd.SIGNATURES}
+    assert set(declared_functions()) <= bound
+
+
+def test_thresholds_match_oracle(lib, oracle_mod):
+    from paper_1301_6082_gb300 import pcpd
+    rng = np.random.default_rng(3)
+    cases = [(0.15, 0.5), (0.11, 0.1), (0.18, 0.9), (1.0, 0.0), (0.0, 1.0), (0.3, 0.0)]
+    cases += [(float(a), float(b)) for a, b in rng.random((200, 2))]
+    for p, d in cases:
+        assert pcpd.thresholds(p, d) == oracle_mod.thresholds(p, d)[:2], (p, d)
+    with pytest.raises(pcpd.PcpdError):
+        pcpd.thresholds(-0.1, 0.5)
+
+
+def test_substep_of_time_matches_oracle(lib, oracle_mod):
+    from paper_1301_6082_gb300 import pcpd
+    for L in (3, 4, 10, 1024, 65536, 1 << 22, 999999):
+        for t in (0, 1, 2, 1000, 10**5, 10**6):
+            assert pcpd.substep_of_time(L, t) == oracle_mod.substep_of_time(L, t)
+
+
+def test_no_cuda_device_fails_loudly(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_1301_6082_gb300 import pcpd
+    with pytest.raises(pcpd.PcpdError) as e:
+        pcpd.Pcpd(64, 64, 0.1, 0.5)
+    assert e.value.code == pcpd.PCPD_ENODEV
+
+
+def test_product_does_not_import_oracle():
+    pkg = os.path.join(ROOT, "paper_1301_6082_gb300")
+    pat = re.compile(r"^\s*(from|import)\s+oracle\b|liboracle|pcpd_oracle", re.M)
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".c")):
+                assert not pat.search(open(os.path.join(dirpath, f)).read()), f

@@ -1,0 +1,199 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle, bit-exact (this is
+integer bit work: lattices and occupation counts must be identical)."""
+import numpy as np
+import pytest
+
+from paper_1301_6082_gb300.workloads import INIT_EMPTY, INIT_FULL, INIT_HALF, log_times
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1301_6082_gb300 import build, pcpd
+    build.build()
+    pcpd.load()
+    return pcpd
+
+
+def _oracle_run(O, L, S, p, d, seed, init, n_end, rec_sub, per_sample=False, group0=0, state=None, n_begin=0):
+    st = O.init_state(L, S, init, seed, group0) if state is None else state
+    tot, ps, _ = O.run(st, p, d, seed, n_begin, n_end, rec_sub, per_sample=per_sample, group0=group0)
+    return st, tot, ps
+
+
+def test_device_philox_matches_oracle(P, oracle_mod):
+    import torch
+    rng = np.random.default_rng(5)
+    n = 100_003
+    ctr = rng.integers(0, 2**32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
+    dc = torch.from_numpy(ctr.view(np.int32)).cuda()
+    out = torch.zeros_like(dc)
+    for seed in (1, 0xDEADBEEFCAFEF00D):
+        P.dev_philox(dc, seed, out, n)
+        got = out.cpu().numpy().view(np.uint32)
+        np.testing.assert_array_equal(got, oracle_mod.philox(ctr, seed))
+
+
+def _scalar_masks(words, td, tda):
+    planes = words[:, 1:]   # P31..P0
+    n = words.shape[0]
+    lanes = np.arange(32, dtype=np.uint64)
+    u = np.zeros((n, 32), dtype=np.uint64)
+    for i in range(32):
+        m = 31 - i
+        u |= ((planes[:, i:i + 1].astype(np.uint64) >> lanes) & 1) << np.uint64(m)
+    D = (u < td)
+    A = (u >= td) & (u < tda)
+    w = (1 << lanes).astype(np.uint64)
+    return (D * w).sum(1).astype(np.uint32), (A * w).sum(1).astype(np.uint32)
+
+
+@pytest.mark.parametrize("td,tda", [(0, 0), (0, 2**32), (2**32, 2**32), (2**31, 2**31 + 1),
+                                    (1, 2), (2**32 - 1, 2**32), (0x19999999, 0x32F1A9FB),
+                                    (0x80000000, 0x93333333), (0xE6666666, 0xEB020C49),
+                                    (12345, 12345), (0x40000000, 0xC0000000)])
+def test_rate_masks_exhaustive_vs_scalar(P, td, tda):
+    # P10: the MSB-first plane compare equals the scalar u < T for every lane; words drawn
+    # so that many lanes share long prefixes with the thresholds (the early-exit paths).
+    import torch
+    rng = np.random.default_rng(td ^ (tda >> 1))
+    n = 20000
+    words = rng.integers(0, 2**32, size=(n, 33), dtype=np.uint64).astype(np.uint32)
+    for t in (td, tda):
+        if t < 2**32:
+            # make lanes of some items equal T on a random number of top bits
+            idx = rng.choice(n, n // 2, replace=False)
+            for it in idx[: n // 4]:
+                k = rng.integers(1, 33)
+                for i in range(k):
+                    m = 31 - i
+                    bit = (t >> m) & 1
+                    lanes = rng.integers(0, 2**32, dtype=np.uint64)
+                    words[it, 1 + i] = np.uint32((words[it, 1 + i] & ~np.uint32(lanes)) | (np.uint32(lanes) if bit else 0))
+    dw = torch.from_numpy(words.view(np.int32)).cuda()
+    dm = torch.zeros((n, 3), dtype=torch.int32, device="cuda")
+    P.dev_rate_masks(dw, td, tda, dm, n)
+    got = dm.cpu().numpy().view(np.uint32)
+    D, A = _scalar_masks(words, td, tda)
+    np.testing.assert_array_equal(got[:, 0], D)
+    np.testing.assert_array_equal(got[:, 1], A)
+    np.testing.assert_array_equal(got[:, 2], words[:, 0])
+
+
+def test_L1024_S64_full_run_bit_exact(P, oracle_mod):
+    # The L=1024, 64-sample, d=.5, p=.15, seed-1 decay run over 2000 MCS, 32 records.
+    L, S, d, p, seed = 1024, 64, 0.5, 0.15, 1
+    ts = log_times(2000, 32)
+    sim = P.Pcpd(L, S, p, d, seed=seed, per_sample=True)
+    sim.run(ts[-1], ts)
+    got = sim.counts()
+    lat = sim.lattice()
+    ps_gpu = np.stack([sim.sample_counts(r) for r in range(len(ts))])
+    subs = [oracle_mod.substep_of_time(L, t) for t in ts]
+    st, tot, ps = _oracle_run(oracle_mod, L, S, p, d, seed, INIT_FULL, subs[-1], subs, per_sample=True)
+    np.testing.assert_array_equal(got, tot)
+    np.testing.assert_array_equal(ps_gpu, ps)
+    np.testing.assert_array_equal(lat, oracle_mod.pack(st))
+    golden = np.loadtxt(__file__.replace("test_gpu_parity.py", "golden/pcpd_L1024_S64.txt"), dtype=np.uint64)
+    np.testing.assert_array_equal(got, golden[:, 2])
+    assert np.allclose(sim.density(), tot / (L * S))
+    assert sim.time_mcs == 2000 and sim.substep == subs[-1]
+
+
+@pytest.mark.parametrize("L,S,p,d,init", [
+    (3, 32, 0.2, 0.3, INIT_HALF), (4, 64, 0.5, 0.0, INIT_FULL), (5, 32, 0.0, 1.0, INIT_HALF),
+    (7, 96, 1.0, 0.0, INIT_FULL), (10, 32, 0.15, 0.5, INIT_HALF), (31, 160, 0.3, 0.7, INIT_HALF),
+    (100, 64, 0.11, 0.1, INIT_FULL), (1000, 32, 0.18, 0.9, INIT_HALF), (3001, 64, 0.25, 0.5, INIT_HALF),
+    (64, 32, 0.15, 0.5, INIT_EMPTY)])
+def test_ring_small_bit_exact(P, oracle_mod, L, S, p, d, init):
+    seed = 1000 + L
+    ts = [0, 1, 2, 5, 13, 40]
+    sim = P.Pcpd(L, S, p, d, seed=seed, init=init, per_sample=True)
+    sim.run(ts[-1], ts)
+    subs = [oracle_mod.substep_of_time(L, t) for t in ts]
+    st, tot, ps = _oracle_run(oracle_mod, L, S, p, d, seed, init, subs[-1], subs, per_sample=True)
+    np.testing.assert_array_equal(sim.counts(), tot)
+    np.testing.assert_array_equal(np.stack([sim.sample_counts(r) for r in range(len(ts))]), ps)
+    np.testing.assert_array_equal(sim.lattice(), oracle_mod.pack(st))
+
+
+@pytest.mark.parametrize("L,seg,tau,threads", [(3000, 1000, 16, 256), (4099, 1500, 37, 128), (20000, 6001, 64, 1024)])
+def test_segmented_plan_bit_exact_and_plan_invariant(P, oracle_mod, L, seg, tau, threads):
+    # Tiles with halos (temporal blocking) and a ragged last tile give the same bits as the
+    # oracle and as the whole-ring plan.
+    S, p, d, seed = 64, 0.15, 0.5, 77
+    ts = [3, 17, 60]
+    a = P.Pcpd(L, S, p, d, seed=seed, init=INIT_HALF, plan_seg_sites=seg, plan_tau=tau, plan_threads=threads)
+    a.run(ts[-1], ts)
+    b = P.Pcpd(L, S, p, d, seed=seed, init=INIT_HALF)
+    b.run(ts[-1], ts)
+    np.testing.assert_array_equal(a.lattice(), b.lattice())
+    np.testing.assert_array_equal(a.counts(), b.counts())
+    subs = [oracle_mod.substep_of_time(L, t) for t in ts]
+    st, tot, _ = _oracle_run(oracle_mod, L, S, p, d, seed, INIT_HALF, subs[-1], subs)
+    np.testing.assert_array_equal(a.counts(), tot)
+    np.testing.assert_array_equal(a.lattice(), oracle_mod.pack(st))
+
+
+def test_resume_from_saved_state_is_exact(P):
+    L, S, p, d, seed = 777, 96, 0.2, 0.4, 3
+    a = P.Pcpd(L, S, p, d, seed=seed, init=INIT_HALF)
+    a.run(30)
+    b = P.Pcpd(L, S, p, d, seed=seed, init=INIT_HALF)
+    b.run(12)
+    saved, n = b.lattice(), b.substep
+    c = P.Pcpd(L, S, p, d, seed=seed, init=INIT_EMPTY)
+    c.set_lattice(saved, n)
+    assert c.time_mcs == 12
+    c.run(18)
+    np.testing.assert_array_equal(a.lattice(), c.lattice())
+
+
+def test_bad_arguments_raise(P):
+    with pytest.raises(P.PcpdError):
+        P.Pcpd(2, 32, 0.1, 0.1)
+    with pytest.raises(P.PcpdError):
+        P.Pcpd(100, 48, 0.1, 0.1)
+    with pytest.raises(P.PcpdError):
+        P.Pcpd(100, 32, 1.5, 0.1)
+    sim = P.Pcpd(100, 32, 0.1, 0.1)
+    with pytest.raises(P.PcpdError):
+        sim.run(10, [5, 5])
+    with pytest.raises(P.PcpdError):
+        sim.run(10, [11])
+    sim.run(10, [10])
+    with pytest.raises(P.PcpdError):
+        sim.run(5, [3])
+
+
+def _sampled_groups_check(P, O, L, S, p, d, seed, n1, groups, plan=None):
+    """Run the GPU for n1 sub-steps at full size, then check the chosen groups against the
+    oracle started from the initial state; then splice: oracle from the GPU state at n1 for
+    a few more sub-steps vs the GPU."""
+    sim = P.Pcpd(L, S, p, d, seed=seed, **(plan or {}))
+    sim.run_substeps(n1)
+    lat1 = sim.lattice()
+    for g in groups:
+        st = O.init_state(L, 32, INIT_FULL, seed, g)
+        O.run(st, p, d, seed, 0, n1, group0=g)
+        np.testing.assert_array_equal(lat1[g], O.pack(st)[0], err_msg=f"group {g} after {n1} sub-steps")
+    dn = 3
+    sim.run_substeps(dn)
+    lat2 = sim.lattice()
+    for g in groups:
+        st = O.unpack(lat1[g:g + 1])
+        O.run(st, p, d, seed, n1, n1 + dn, group0=g)
+        np.testing.assert_array_equal(lat2[g], O.pack(st)[0], err_msg=f"splice group {g}")
+
+
+@pytest.mark.parametrize("d,p", [(0.1, 0.11), (0.5, 0.15), (0.9, 0.18)])
+def test_L65536_S4096_sampled_groups(P, oracle_mod, d, p):
+    _sampled_groups_check(P, oracle_mod, 65536, 4096, p, d, 1, 4, [0, 5, 127])
+
+
+def test_L4194304_S1024_sampled_groups(P, oracle_mod):
+    _sampled_groups_check(P, oracle_mod, 1 << 22, 1024, 0.15, 0.5, 1, 2, [0, 31])
