@@ -1,0 +1,327 @@
+#!/usr/bin/env python3
+"""Benchmark of the bit-sliced PCPD sweep on GB300.
+
+Workload (the single-GPU configuration of the headline metric): PCPD on a periodic lattice of
+L = 65536 sites, 4096 samples bit-sliced into 32-bit words (128 groups; the "uint64 per site"
+of the workload is two such groups), fully occupied start, three runs (d, p) = (0.1, 0.11),
+(0.5, 0.15), (0.9, 0.18), Philox seed 1, records at the 100 log-spaced times of a 10^6-MCS
+run.  One bench step advances each of the three runs by --mcs-per-step MCS: consecutive
+segments of the same 10^6-MCS runs, with the records that fall inside the segment.
+
+Metric: attempted site updates per second (sample x window attempts; S*K per sub-step).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (torchrun): independent replicas, one per GPU, with disjoint seeds; no data-path
+collective (the runs do not exchange anything); value = all ranks' attempts / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1301_6082_gb300.workloads import SMEM_L65536, log_times  # noqa: E402
+
+METRIC = "attempted site updates/s"
+UNIT = "attempts/s"
+
+
+def algorithmic_ops_per_item(t_d: int, t_da: int):
+    """Algorithmic integer operations per (window, 32-sample group) item of the method:
+    40 per Philox4x32-10 block (10 rounds x (2 wide multiplies + 2 three-input XORs)) times
+    the expected number of blocks under the per-item MSB-first early exit, 2 per expected
+    plane (one three-input logic op per plane per threshold), 11 for the window logic and 6
+    shared-memory loads/stores.  Returns (ops, expected blocks, expected planes)."""
+    two32 = 1 << 32
+
+    def p_open(k):  # P(the item is still undecided after k planes)
+        cells = set()
+        for T in (t_d, t_da):
+            if T >= two32 or T == 0:
+                continue
+            low = T & ((1 << (32 - k)) - 1) if k < 32 else 0
+            if low:
+                cells.add(T >> (32 - k))
+        return 1.0 - (1.0 - len(cells) * 2.0 ** -k) ** 32
+    planes = sum(p_open(k) for k in range(32))
+    blocks = 1.0 + sum(p_open(k) for k in (3, 7, 11, 15, 19, 23, 27, 31))
+    return 40.0 * blocks + 2.0 * planes + 11.0 + 6.0, blocks, planes
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_cpu_sample(budget_groups: int = 16, substeps: int = 300):
+    """The oracle as it stands, on a bounded sample of the workload: `budget_groups` groups
+    (32 samples each) of the L=65536 lattice at (d,p) = (0.5, 0.15), `substeps` sub-steps from
+    the full start, threads = min(host cores, groups)."""
+    from oracle import oracle as O
+    L = SMEM_L65536["L"]
+    S = 32 * budget_groups
+    d, p = 0.5, 0.15
+    cores = min(os.cpu_count() or 1, budget_groups)
+    st = O.init_state(L, S, O.MODE_FULL, 1)
+    t0 = time.perf_counter()
+    O.run(st, p, d, 1, 0, substeps, threads=cores)
+    dt = time.perf_counter() - t0
+    attempts = S * (L // 3) * substeps
+    return {"value": attempts / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{budget_groups} groups ({S} samples) of L={L}, d=0.5 p=0.15, {substeps} sub-steps "
+                      f"from full ({attempts:.3e} attempts, {dt:.1f} s)"}
+
+
+def reference_arm(args, world, rank):
+    """The oracle timed on the host cores, one bounded sample of the workload per step."""
+    if rank != 0:
+        return 0
+    groups, subs = 8, 60
+    res = None
+    times = []
+    for i in range(args.warmup + args.steps):
+        r = run_cpu_sample(groups, subs)
+        if i >= args.warmup:
+            times.append(r)
+        res = r
+    vals = [r["value"] for r in times]
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * (32 * groups * (SMEM_L65536["L"] // 3) * subs) / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic",
+            "config": {"workload": SMEM_L65536["name"], "L": SMEM_L65536["L"], "samples": SMEM_L65536["S"],
+                       "note": "each step: the CPU oracle on a bounded sample of the workload"},
+            "cpu_baseline": {"kind": "oracle", "cores": res["cores"], "sample": res["sample"], "value": value,
+                             "unit": UNIT},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mcs-per-step", type=int, default=2000)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        return reference_arm(args, world, rank)
+
+    import numpy as np
+    import torch
+    from paper_1301_6082_gb300 import build as B
+    B.build()
+    from paper_1301_6082_gb300 import pcpd
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+    W = SMEM_L65536
+    L, S = W["L"], W["S"]
+    K_win = L // 3
+    runs = W["runs"]
+    rec_all = log_times(W["mcs"], W["n_rec"])
+    stream = torch.cuda.Stream()
+    sims = []
+    for i, (d, p) in enumerate(runs):
+        sims.append(pcpd.Pcpd(L, S, p, d, seed=W["seed"] + 1000003 * rank, stream=stream))
+    ops_item = []
+    for d, p in runs:
+        td, tda = pcpd.thresholds(p, d)
+        ops_item.append(algorithmic_ops_per_item(td, tda))
+
+    mcs = args.mcs_per_step
+
+    def step(sim_list, t0):
+        recs = [t for t in rec_all if t0 < t <= t0 + mcs]
+        for s in sim_list:
+            s.run(mcs, recs)
+
+    t_now = 0
+    for _ in range(args.warmup):
+        step(sims, t_now)
+        t_now += mcs
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sub0 = [s.substep for s in sims]
+    launches0 = pcpd.kernel_launches()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step(sims, t_now)
+        t_now += mcs
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    launches = pcpd.kernel_launches() - launches0
+    ms = ev0.elapsed_time(ev1)
+    subs = [s.substep - a for s, a in zip(sims, sub0)]
+    attempts = sum(S * K_win * n for n in subs)
+    alg_ops = sum(S // 32 * K_win * n * o[0] for n, o in zip(subs, ops_item))
+    if dist:
+        t = torch.tensor([ms, attempts, alg_ops], dtype=torch.float64, device="cuda")
+        tm = t.clone()
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        ms_max, attempts_all, alg_all = tm[0].item(), t[1].item(), t[2].item()
+    else:
+        ms_max, attempts_all, alg_all = ms, attempts, alg_ops
+    value = attempts_all / (ms_max / 1e3)
+
+    # roofline of the dominant kernel (the tile sweep): integer issue slots
+    props = torch.cuda.get_device_properties(local)
+    sm_count = props.multi_processor_count
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = sm_count * 4 * 32 * sm_max_mhz * 1e6 / 1e12   # T lane-ops/s
+    achieved = (alg_ops / (ms / 1e3)) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "k_sweep_tile (segmented tiles, tau=128)",
+                "peak_note": f"{sm_count} SMs x 4 SMSPs x 32 lanes x {sm_max_mhz:.0f} MHz issue slots (derived)",
+                "ops_per_attempt": [round(o[0] / 32, 3) for o in ops_item]}
+
+    # end to end through the public API with host buffers (pinned), host<->device in the region
+    e2e = None
+    if args.e2e_steps > 0:
+        host = [torch.empty((S // 32, L), dtype=torch.int32, pin_memory=True) for _ in sims]
+        for s, hb in zip(sims, host):
+            hb.numpy().view(np.uint32)[...] = s.lattice()
+        n_before = [s.substep for s in sims]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        att_e2e, h2d, d2h = 0, 0, 0
+        for _ in range(args.e2e_steps):
+            for s, hb, nb in zip(sims, host, n_before):
+                arr = hb.numpy().view(np.uint32)
+                s.set_lattice(arr, s.substep)
+                h2d += arr.nbytes
+                n0 = s.substep
+                recs = [t for t in rec_all if s.time_mcs < t <= s.time_mcs + mcs]
+                s.run(mcs, recs)
+                rho = s.density()
+                d2h += rho.nbytes
+                arr[...] = s.lattice()
+                d2h += arr.nbytes
+                att_e2e += S * K_win * (s.substep - n0)
+        dt = time.perf_counter() - t0
+        e2e_val = att_e2e / dt
+        if dist:
+            t = torch.tensor([dt, att_e2e], dtype=torch.float64, device="cuda")
+            tm = t.clone()
+            dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+            dist.all_reduce(t, op=dist.ReduceOp.SUM)
+            e2e_val = t[1].item() / tm[0].item()
+        e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d // args.e2e_steps,
+               "d2h_bytes_per_step": d2h // args.e2e_steps,
+               "note": "pcpd_set_lattice from pinned host memory + pcpd_run + pcpd_density + pcpd_get_lattice per run per step"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = run_cpu_sample()
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+                "config": {"workload": W["name"], "L": L, "samples": S,
+                           "runs_d_p": [list(r) for r in runs], "run_mcs": W["mcs"],
+                           "mcs_per_step": mcs, "step": "each of the 3 runs advances mcs_per_step MCS "
+                           "(consecutive segments of the 1e6-MCS runs, records included)",
+                           "records": W["n_rec"], "seed": W["seed"], "init": "full",
+                           "l2": "inputs larger than L2: 3 lattices x 2 buffers x 32 MiB = 192 MiB, streamed per tile epoch",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "gpu_launches": launches}
+        print(json.dumps(line), flush=True)
+    for s in sims:
+        s.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

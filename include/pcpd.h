@@ -125,6 +125,10 @@ void pcpd_destroy(pcpd_t *h);
 /* Message for the last error on this thread ("" if none). */
 const char *pcpd_last_error(void);
 
+/* Number of CUDA kernels this library has launched in this process so far (all handles,
+ * all threads).  Lets a caller count the device work of a region. */
+unsigned long long pcpd_kernel_launches(void);
+
 /* Integer thresholds of the rates of Eq. (1): T_D = min(2^32, floor(d*2^32)),
  * T_DA = min(2^32, T_D + floor(p*(1-d)*2^32)), IEEE double, no contraction.  A sample with
  * draw u diffuses if u < T_D, else annihilates an occupied bond if u < T_DA, else fissions. */

@@ -2,6 +2,7 @@
 // time bookkeeping, tile plans and kernel launches for the bit-sliced PCPD sweep.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -15,6 +16,9 @@
 namespace {
 
 thread_local std::string g_err;
+
+// Kernels this library has launched in this process (all threads).
+std::atomic<unsigned long long> g_launches{0};
 
 int fail(int code, const char *fmt, ...) {
   char buf[512];
@@ -264,6 +268,7 @@ int launch_sweep(pcpd_t *h, uint64_t n_end, const std::vector<uint64_t> &subs, s
       h->cur = 1 - h->cur;
     }
     CU(cudaGetLastError());
+    g_launches.fetch_add(1, std::memory_order_relaxed);
     ri = rj;
     n = nb;
   }
@@ -276,6 +281,8 @@ int launch_sweep(pcpd_t *h, uint64_t n_end, const std::vector<uint64_t> &subs, s
 extern "C" {
 
 const char *pcpd_last_error(void) { return g_err.c_str(); }
+
+unsigned long long pcpd_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 int pcpd_thresholds(double p, double d, uint64_t *t_d, uint64_t *t_da) {
   if (!t_d || !t_da) return fail(PCPD_EINVAL, "NULL output");
@@ -340,6 +347,7 @@ int pcpd_create_ex(const pcpd_params *prm, pcpd_t **out) {
   pcpdk::k_init<<<1024, 256, 0, h->stream>>>(h->buf[0], h->L, h->G, h->init, h->k0, h->k1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return bail(fail(PCPD_ECUDA, "init launch: %s", cudaGetErrorString(e)));
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   *out = h;
   return PCPD_OK;
 }
@@ -396,6 +404,7 @@ int pcpd_run(pcpd_t *h, uint64_t steps_mcs, const uint64_t *times, size_t n_time
     pcpdk::k_count<<<h->G, 256, 0, h->stream>>>(h->buf[h->cur], h->L, h->S, h->d_rec_total + slot,
                                                  h->per_sample ? h->d_rec_sample + slot * (size_t)h->S : nullptr);
     CU(cudaGetLastError());
+    g_launches.fetch_add(1, std::memory_order_relaxed);
     ++slot;
   }
   if (!subs.empty()) {

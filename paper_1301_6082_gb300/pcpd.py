@@ -52,6 +52,7 @@ SIGNATURES = [
     ("pcpd_sync", C.c_int, [C.c_void_p]),
     ("pcpd_destroy", None, [C.c_void_p]),
     ("pcpd_last_error", C.c_char_p, []),
+    ("pcpd_kernel_launches", C.c_ulonglong, []),
     ("pcpd_thresholds", C.c_int, [C.c_double, C.c_double, _u64p, _u64p]),
     ("pcpd_substep_of_time", C.c_uint64, [C.c_uint32, C.c_uint64]),
     ("pcpd_dev_philox", C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_size_t, C.c_void_p]),
@@ -79,6 +80,10 @@ def load(path: str = LIB_PATH):
 def _check(rc: int):
     if rc != PCPD_OK:
         raise PcpdError(rc, load().pcpd_last_error().decode())
+
+
+def kernel_launches() -> int:
+    return int(load().pcpd_kernel_launches())
 
 
 def thresholds(p: float, d: float):
