@@ -80,6 +80,13 @@ pcpdk::Thresholds split_thresholds(uint64_t td, uint64_t tda) {
   T.tda_full = tda >= kTwo32;
   T.td = (uint32_t)(T.td_full ? 0u : td);
   T.tda = (uint32_t)(T.tda_full ? 0u : tda);
+  // lowest plane that matters: the lowest set bit of T (none for T = 0 or 2^32)
+  T.lo_d = (T.td_full || T.td == 0u) ? 32u : (uint32_t)__builtin_ctz(T.td);
+  T.lo_da = (T.tda_full || T.tda == 0u) ? 32u : (uint32_t)__builtin_ctz(T.tda);
+  for (int m = 0; m < 32; ++m) {
+    T.tmD[m] = (!T.td_full && ((T.td >> m) & 1u)) ? 0xFFFFFFFFu : 0u;
+    T.tmA[m] = (!T.tda_full && ((T.tda >> m) & 1u)) ? 0xFFFFFFFFu : 0u;
+  }
   return T;
 }
 
@@ -103,7 +110,7 @@ int smem_optin(int *bytes) {
 }
 
 // Static shared memory of the tile kernel (phase buffer + reduction slots), with margin.
-constexpr size_t kStaticSmem = sizeof(uint32_t) * pcpdk::kPhiChunk + 33 * sizeof(unsigned int) + 256;
+constexpr size_t kStaticSmem = sizeof(uint32_t) * pcpdk::kPhiChunk + 34 * sizeof(unsigned int) + 256;
 
 }  // namespace
 
@@ -141,7 +148,7 @@ int make_plan(pcpd_t *h, const pcpd_params *prm) {
   int optin = 0;
   int rc = smem_optin(&optin);
   if (rc) return rc;
-  const size_t avail_words = ((size_t)optin - kStaticSmem) / 4;
+  const size_t avail_words = ((size_t)optin - kStaticSmem) / 4 - pcpdk::sweep_queue_words(32);
   const uint32_t L = h->L;
   const uint32_t seg_override = prm ? prm->plan_seg_sites : 0;
   if (seg_override == 0 && L <= avail_words) {
@@ -149,7 +156,6 @@ int make_plan(pcpd_t *h, const pcpd_params *prm) {
     h->core = L;
     h->halo = 0;
     h->n_seg = 1;
-    h->dyn_smem = (size_t)L * 4;
     uint32_t want = (h->K + 31u) / 32u * 32u;
     if (want > 1024u) want = 1024u;
     if (want < 32u) want = 32u;
@@ -173,7 +179,6 @@ int make_plan(pcpd_t *h, const pcpd_params *prm) {
     if (tile > avail_words) return fail(PCPD_EINVAL, "tile of %zu sites exceeds shared memory", tile);
     if (h->n_seg < 2 || tile + 12 > L)
       return fail(PCPD_EINVAL, "segmented plan needs >= 2 tiles each shorter than L-12 (L=%u, core=%u, halo=%u)", L, core, h->halo);
-    h->dyn_smem = tile * 4;
     h->threads = 1024;
   }
   if (prm && prm->plan_threads) {
@@ -181,6 +186,10 @@ int make_plan(pcpd_t *h, const pcpd_params *prm) {
       return fail(PCPD_EINVAL, "plan_threads must be a multiple of 32 and <= 1024");
     h->threads = prm->plan_threads;
   }
+  const size_t tile_words = h->ring ? (size_t)L : (size_t)h->core + 2u * h->halo;
+  h->dyn_smem = 4 * (tile_words + pcpdk::sweep_queue_words((int)(h->threads / 32)));
+  if (h->dyn_smem + kStaticSmem > (size_t)optin)
+    return fail(PCPD_EINVAL, "tile of %zu sites plus queues exceeds shared memory", tile_words);
   return PCPD_OK;
 }
 
@@ -233,6 +242,7 @@ int launch_sweep(pcpd_t *h, uint64_t n_end, const std::vector<uint64_t> &subs, s
   P.S = h->S;
   P.k0 = h->k0;
   P.k1 = h->k1;
+  P.rk = pcpdk::make_round_keys(h->k0, h->k1);
   P.T = h->T;
   P.core = h->core;
   P.halo = h->halo;

@@ -40,12 +40,84 @@ __device__ __forceinline__ void philox4x32_10(uint32_t &x0, uint32_t &x1, uint32
   }
 }
 
+// Round keys of Philox4x32-10 for one seed: key r = (k0 + r*W0, k1 + r*W1), r = 0..9.
+struct RoundKeys {
+  uint32_t k0[10], k1[10];
+};
+
+__host__ __device__ inline RoundKeys make_round_keys(uint32_t k0, uint32_t k1) {
+  RoundKeys rk;
+  for (int r = 0; r < 10; ++r) {
+    rk.k0[r] = k0 + (uint32_t)r * kPhiloxW0;
+    rk.k1[r] = k1 + (uint32_t)r * kPhiloxW1;
+  }
+  return rk;
+}
+
+// Ten Philox4x32 rounds with the keys taken from a RoundKeys table (kernel constants).
+__device__ __forceinline__ void philox4x32_10_rk(uint32_t &x0, uint32_t &x1, uint32_t &x2,
+                                                 uint32_t &x3, const RoundKeys &rk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)x0 * kPhiloxM0;
+    const uint64_t p1 = (uint64_t)x2 * kPhiloxM1;
+    x0 = (uint32_t)(p1 >> 32) ^ x1 ^ rk.k0[r];
+    x1 = (uint32_t)p1;
+    x2 = (uint32_t)(p0 >> 32) ^ x3 ^ rk.k1[r];
+    x3 = (uint32_t)p0;
+  }
+}
+
 // Thresholds of one instance, pre-split for the plane compare.  A threshold T in [0, 2^32]:
 // `full` = T == 2^32 (every draw is below it), else `t` = T.
+// lo_d / lo_da: the lowest plane that still matters for T (T's bits below it are all zero,
+// so a lane whose prefix equals T's is already known to satisfy u >= T); 32 when no plane
+// matters (T = 0 or T = 2^32).
 struct Thresholds {
   uint32_t td, tda;
   uint32_t td_full, tda_full;
+  uint32_t lo_d, lo_da;
+  uint32_t tmD[32], tmA[32];   // tm[m] = all ones if bit m of T is set, else 0
 };
+
+// Compare state of 32 lanes against one threshold: `lt` = decided u < T, `eq` = undecided
+// (u's planes so far equal T's bits); lanes in neither are decided u >= T.
+struct Cmp {
+  uint32_t lt, eq;
+};
+
+__device__ __forceinline__ Cmp cmp_init(uint32_t t, uint32_t full) {
+  Cmp c;
+  c.lt = full ? 0xFFFFFFFFu : 0u;
+  c.eq = (full || t == 0u) ? 0u : 0xFFFFFFFFu;
+  return c;
+}
+
+// Fold the K planes m_hi, m_hi-1, ..., m_hi-K+1 (words w[0..K-1]) into the compare state.
+// Within the group: eq_g = AND over planes of (P == T bit), and lt_g = (planes < T's bits)
+// by a borrow chain run least-significant plane first, b' = (~P & t) | (~(P ^ t) & b) --
+// each a single three-input logic operation with T's bit mask t as a kernel constant.
+// Then lt |= eq & lt_g and eq &= eq_g: lanes still equal above the group are decided by it.
+template <int K>
+__device__ __forceinline__ void cmp_group(Cmp &c, const uint32_t (&w)[K], const uint32_t *tm,
+                                          int m_hi) {
+  uint32_t eq = c.eq, b = 0u;
+#pragma unroll
+  for (int q = 0; q < K; ++q) eq &= ~(w[q] ^ tm[m_hi - q]);
+#pragma unroll
+  for (int q = K - 1; q >= 0; --q) {
+    const uint32_t t = tm[m_hi - q], P = w[q];
+    b = (~P & t) | (~(P ^ t) & b);
+  }
+  c.lt |= c.eq & b;
+  c.eq = eq;
+}
+
+// True while some lane is undecided after the planes down to m_lo and T has a set bit below
+// m_lo (if T's lower bits are all zero, a lane equal so far is already known u >= T).
+__device__ __forceinline__ bool cmp_open2(const Cmp &c, uint32_t lo, int m_lo) {
+  return c.eq != 0u && (uint32_t)m_lo > lo;
+}
 
 // Less/greater state of the MSB-first compare of 32 lanes against one threshold: lanes in
 // `lt` are decided u < T, lanes in `gt` decided u >= T, the rest match T's bits so far.
@@ -54,12 +126,18 @@ __device__ __forceinline__ void cmp_plane(uint32_t &lt, uint32_t &gt, uint32_t p
   else      gt |= plane & ~lt;     // T bit 0: an undecided lane with bit 1 is above T
 }
 
-// True while some lane is undecided against T after the planes down to `m` (inclusive) and T
-// still has a non-zero bit below m (if all of T's lower bits are zero, a lane whose prefix
-// equals T's is already known to satisfy u >= T).
-__device__ __forceinline__ bool cmp_open(uint32_t lt, uint32_t gt, uint32_t t, bool full, int m) {
-  const uint32_t low = (m == 0) ? 0u : (t & ((1u << m) - 1u));
-  return !full && low != 0u && ((lt | gt) != 0xFFFFFFFFu);
+// Plane m of threshold T.  Planes below T's lowest set bit change nothing that matters (a
+// lane that still equals T's prefix there is >= T either way), so they need no test.
+__device__ __forceinline__ void cmp_plane_if(uint32_t &lt, uint32_t &gt, uint32_t plane,
+                                             uint32_t t, uint32_t lo, int m) {
+  (void)lo;
+  cmp_plane(lt, gt, plane, (t >> m) & 1u);
+}
+
+// True while some lane is undecided against T after the planes down to m (inclusive) and T
+// still has a non-zero bit below m.
+__device__ __forceinline__ bool cmp_open(uint32_t lt, uint32_t gt, uint32_t lo, int m) {
+  return (uint32_t)m > lo && ((lt | gt) != 0xFFFFFFFFu);
 }
 
 // Rate masks of one (window k, sub-step n, group g): D = lanes with u < T_D (diffuse),
@@ -70,50 +148,38 @@ struct Masks {
   uint32_t D, A, O;
 };
 
-__device__ __forceinline__ Masks rate_masks(uint32_t k, uint32_t n, uint32_t g, uint32_t k0,
-                                            uint32_t k1, const Thresholds &T) {
+__device__ __forceinline__ Masks rate_masks(uint32_t k, uint32_t n, uint32_t g,
+                                            const RoundKeys &rk, const Thresholds &T) {
   uint32_t ltD = T.td_full ? 0xFFFFFFFFu : 0u, gtD = (!T.td_full && T.td == 0u) ? 0xFFFFFFFFu : 0u;
   uint32_t ltA = T.tda_full ? 0xFFFFFFFFu : 0u, gtA = (!T.tda_full && T.tda == 0u) ? 0xFFFFFFFFu : 0u;
   uint32_t O;
   {
     uint32_t x0 = k, x1 = n, x2 = g, x3 = (kTagDyn << 28) | 0u;
-    philox4x32_10(x0, x1, x2, x3, k0, k1);
+    philox4x32_10_rk(x0, x1, x2, x3, rk);
     O = x0;
-    if (!T.td_full) {
-      cmp_plane(ltD, gtD, x1, (T.td >> 31) & 1u);
-      cmp_plane(ltD, gtD, x2, (T.td >> 30) & 1u);
-      cmp_plane(ltD, gtD, x3, (T.td >> 29) & 1u);
-    }
-    if (!T.tda_full) {
-      cmp_plane(ltA, gtA, x1, (T.tda >> 31) & 1u);
-      cmp_plane(ltA, gtA, x2, (T.tda >> 30) & 1u);
-      cmp_plane(ltA, gtA, x3, (T.tda >> 29) & 1u);
-    }
+    cmp_plane_if(ltD, gtD, x1, T.td, T.lo_d, 31);
+    cmp_plane_if(ltD, gtD, x2, T.td, T.lo_d, 30);
+    cmp_plane_if(ltD, gtD, x3, T.td, T.lo_d, 29);
+    cmp_plane_if(ltA, gtA, x1, T.tda, T.lo_da, 31);
+    cmp_plane_if(ltA, gtA, x2, T.tda, T.lo_da, 30);
+    cmp_plane_if(ltA, gtA, x3, T.tda, T.lo_da, 29);
   }
 #pragma unroll
   for (int b = 1; b <= 8; ++b) {
     const int m_prev = 33 - 4 * b;  // lowest plane consumed so far
-    if (!cmp_open(ltD, gtD, T.td, T.td_full, m_prev) &&
-        !cmp_open(ltA, gtA, T.tda, T.tda_full, m_prev))
-      break;
+    if (!cmp_open(ltD, gtD, T.lo_d, m_prev) && !cmp_open(ltA, gtA, T.lo_da, m_prev)) break;
     uint32_t x0 = k, x1 = n, x2 = g, x3 = (kTagDyn << 28) | (uint32_t)b;
-    philox4x32_10(x0, x1, x2, x3, k0, k1);
+    philox4x32_10_rk(x0, x1, x2, x3, rk);
     const int m0 = 32 - 4 * b;  // plane of x0
-    if (!T.td_full) {
-      cmp_plane(ltD, gtD, x0, (T.td >> m0) & 1u);
-      if (b < 8) {
-        cmp_plane(ltD, gtD, x1, (T.td >> (m0 - 1)) & 1u);
-        cmp_plane(ltD, gtD, x2, (T.td >> (m0 - 2)) & 1u);
-        cmp_plane(ltD, gtD, x3, (T.td >> (m0 - 3)) & 1u);
-      }
-    }
-    if (!T.tda_full) {
-      cmp_plane(ltA, gtA, x0, (T.tda >> m0) & 1u);
-      if (b < 8) {
-        cmp_plane(ltA, gtA, x1, (T.tda >> (m0 - 1)) & 1u);
-        cmp_plane(ltA, gtA, x2, (T.tda >> (m0 - 2)) & 1u);
-        cmp_plane(ltA, gtA, x3, (T.tda >> (m0 - 3)) & 1u);
-      }
+    cmp_plane_if(ltD, gtD, x0, T.td, T.lo_d, m0);
+    cmp_plane_if(ltA, gtA, x0, T.tda, T.lo_da, m0);
+    if (b < 8) {
+      cmp_plane_if(ltD, gtD, x1, T.td, T.lo_d, m0 - 1);
+      cmp_plane_if(ltD, gtD, x2, T.td, T.lo_d, m0 - 2);
+      cmp_plane_if(ltD, gtD, x3, T.td, T.lo_d, m0 - 3);
+      cmp_plane_if(ltA, gtA, x1, T.tda, T.lo_da, m0 - 1);
+      cmp_plane_if(ltA, gtA, x2, T.tda, T.lo_da, m0 - 2);
+      cmp_plane_if(ltA, gtA, x3, T.tda, T.lo_da, m0 - 3);
     }
   }
   Masks r;
@@ -131,10 +197,12 @@ __device__ __forceinline__ void window_update(uint32_t &a, uint32_t &b, uint32_t
                                               const Masks &m) {
   const uint32_t q = (m.O & c) | (~m.O & a);   // partner of b
   const uint32_t t = (m.O & a) | (~m.O & c);   // fission target
-  const uint32_t F = ~(m.D | m.A);
-  const uint32_t nb = (m.D & q) | (~m.D & b & ~(m.A & q));
-  const uint32_t nq = (m.D & b) | (~m.D & q & ~(m.A & b));
-  const uint32_t nt = t | (F & b & q);
+  const uint32_t pair = b & q;                 // occupied bond
+  const uint32_t xb = b ^ (m.A & pair);        // b after an annihilation
+  const uint32_t xq = q ^ (m.A & pair);        // partner after an annihilation
+  const uint32_t nb = (m.D & q) | (~m.D & xb); // a diffusion swaps b and its partner
+  const uint32_t nq = (m.D & b) | (~m.D & xq);
+  const uint32_t nt = t | (pair & ~(m.D | m.A)); // fission fills the target
   a = (m.O & nt) | (~m.O & nq);
   c = (m.O & nq) | (~m.O & nt);
   b = nb;
@@ -164,6 +232,7 @@ struct SweepParams {
   uint32_t core;                // core sites per tile (RING: L)
   uint32_t halo;                // H (RING: 0)
   uint32_t k0, k1;              // Philox key
+  RoundKeys rk;                 // its round keys
   Thresholds T;
   uint32_t n_begin, n_end;      // sub-steps [n_begin, n_end)
   const uint32_t *rec_sub;      // records: state after rec_sub[r] sub-steps, in (n_begin, n_end]
@@ -206,11 +275,97 @@ __device__ __forceinline__ void tile_count(const uint32_t *sm, uint32_t y0, uint
   __syncthreads();
 }
 
+// Per-sub-step geometry of the windows a tile computes.  Candidate i is window k(i) with
+// first site at tile index y(i); RING: k = i, y = (phi + 3i) mod L; SEGMENT: k = k_lo + i (mod K)
+// and y = y_first + 3i, plus the idle gap L - 3K once k wraps from K-1 to 0.
+struct Geometry {
+  uint32_t phi, n_cand, k_lo, gap;
+  int y_first;
+  uint32_t lo, hi;
+};
+
+template <bool RING>
+__device__ __forceinline__ bool candidate(const Geometry &G, uint32_t i, uint32_t L, uint32_t K,
+                                          uint32_t &k, uint32_t &ia, uint32_t &ib, uint32_t &ic) {
+  if (i >= G.n_cand) return false;
+  if (RING) {
+    k = i;
+    ia = G.phi + 3u * i;
+    if (ia >= L) ia -= L;
+    ib = ia + 1u;
+    if (ib >= L) ib -= L;
+    ic = ib + 1u;
+    if (ic >= L) ic -= L;
+    return true;
+  } else {
+    k = G.k_lo + i;
+    int y = G.y_first + 3 * (int)i;
+    if (k >= K) {
+      k -= K;
+      y += (int)G.gap;
+    }
+    if (y < (int)G.lo || y + 2 >= (int)G.hi) return false;
+    ia = (uint32_t)y;
+    ib = ia + 1u;
+    ic = ia + 2u;
+    return true;
+  }
+}
+
+// Every window draws blocks 0-2 (O and planes 31..21) up front: with 32 lanes per item a
+// block-by-block early exit would make the whole warp wait for its slowest lane.  The few
+// windows still undecided after plane 21 (about 3% for generic thresholds) are deferred to a
+// per-CTA list and finished after the first pass of the sub-step with blocks 3..8, so their
+// extra blocks run on compacted lanes.  Entries keep the candidate index, O and the compare
+// state.
+constexpr int kQ3Cap = 1024;  // per CTA; overflow is processed in place
+constexpr int kQFields = 6;   // i, O, ltD, eqD, ltA, eqA
+
+__host__ __device__ constexpr size_t sweep_queue_words(int nwarps) {
+  return (void)nwarps, (size_t)kQFields * kQ3Cap;
+}
+
+// Finish an item from block 3 on: draw blocks 3.. until both compares are closed.
+__device__ __forceinline__ void finish_from3(uint32_t k, uint32_t n, uint32_t g,
+                                             const RoundKeys &rk, const Thresholds &T,
+                                             Cmp &cD, Cmp &cA) {
+#pragma unroll
+  for (int b = 3; b <= 8; ++b) {
+    const int m_prev = 33 - 4 * b;
+    if (!cmp_open2(cD, T.lo_d, m_prev) && !cmp_open2(cA, T.lo_da, m_prev)) break;
+    uint32_t x0 = k, x1 = n, x2 = g, x3 = (kTagDyn << 28) | (uint32_t)b;
+    philox4x32_10_rk(x0, x1, x2, x3, rk);
+    if (b < 8) {
+      const uint32_t w[4] = {x0, x1, x2, x3};
+      cmp_group<4>(cD, w, T.tmD, 32 - 4 * b);
+      cmp_group<4>(cA, w, T.tmA, 32 - 4 * b);
+    } else {
+      const uint32_t w[1] = {x0};
+      cmp_group<1>(cD, w, T.tmD, 0);
+      cmp_group<1>(cA, w, T.tmA, 0);
+    }
+  }
+}
+
+__device__ __forceinline__ void apply_window(uint32_t *sm, uint32_t ia, uint32_t ib, uint32_t ic,
+                                             uint32_t O, uint32_t ltD, uint32_t ltA) {
+  Masks m;
+  m.D = ltD;
+  m.A = ltA & ~ltD;   // T_D <= u < T_DA
+  m.O = O;
+  uint32_t a = sm[ia], b = sm[ib], c = sm[ic];
+  window_update(a, b, c, m);
+  sm[ia] = a;
+  sm[ib] = b;
+  sm[ic] = c;
+}
+
 template <bool RING>
 __global__ void __launch_bounds__(1024, 1) k_sweep_tile(const SweepParams P) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ uint32_t s_phi[kPhiChunk];
   __shared__ unsigned int s_red[33];
+  __shared__ unsigned int s_q3n;
 
   const uint32_t g = blockIdx.y;
   const uint32_t L = P.L, K = P.K;
@@ -220,6 +375,11 @@ __global__ void __launch_bounds__(1024, 1) k_sweep_tile(const SweepParams P) {
   const uint32_t tile_len = core_len + 2u * H;
   const uint32_t base = RING ? 0u : (uint32_t)(((uint64_t)s0 + L - H) % L);
   const uint32_t h = (32u * g) / 128u;
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+
+  // the deferred-window list follows the tile words: Q3[field][kQ3Cap]
+  const uint32_t tile_words = RING ? L : P.core + 2u * P.halo;
+  uint32_t *q3 = smem + tile_words;
 
   const uint32_t *src = P.src + (size_t)g * L;
   for (uint32_t y = threadIdx.x; y < tile_len; y += blockDim.x) {
@@ -230,53 +390,104 @@ __global__ void __launch_bounds__(1024, 1) k_sweep_tile(const SweepParams P) {
   for (uint32_t t = threadIdx.x; t <= 32u; t += blockDim.x) s_red[t] = 0;
   __syncthreads();
 
-  uint32_t lo = 0, hi = tile_len;   // valid region of the tile (SEGMENT mode)
-  uint32_t r = 0;                   // next record
+  Geometry G;
+  G.lo = 0;
+  G.hi = tile_len;
+  G.gap = L - 3u * K;
+  uint32_t r = 0;  // next record
   for (uint32_t n = P.n_begin; n < P.n_end; ++n) {
     const uint32_t j = (n - P.n_begin) % kPhiChunk;
     if (j == 0) {
       for (uint32_t t = threadIdx.x; t < kPhiChunk; t += blockDim.x)
         s_phi[t] = phase_of(n + t, h, L, P.k0, P.k1);
-      __syncthreads();
     }
-    const uint32_t phi = s_phi[j];
+    if (threadIdx.x == 0) s_q3n = 0;
+    __syncthreads();
+    G.phi = s_phi[j];
+    uint32_t w_lo = 0;
     if (RING) {
-      for (uint32_t k = threadIdx.x; k < K; k += blockDim.x) {
-        uint32_t ia = phi + 3u * k;
-        if (ia >= L) ia -= L;
-        uint32_t ib = ia + 1u;
-        if (ib >= L) ib -= L;
-        uint32_t ic = ib + 1u;
-        if (ic >= L) ic -= L;
-        uint32_t a = smem[ia], b = smem[ib], c = smem[ic];
-        const Masks m = rate_masks(k, n, g, P.k0, P.k1, P.T);
-        window_update(a, b, c, m);
-        smem[ia] = a;
-        smem[ib] = b;
-        smem[ic] = c;
-      }
+      G.n_cand = K;
     } else {
-      // window coordinate of tile position y: w(y) = (base + y - phi) mod L; a window starts
-      // at every w = 3k < 3K.  Candidates: from the window holding position lo onwards.
-      const uint32_t w_lo = (uint32_t)(((uint64_t)base + lo + L - phi) % L);
-      const uint32_t k_lo = (w_lo < 3u * K) ? w_lo / 3u : 0u;
-      const uint32_t n_cand = (hi - lo) / 3u + 2u;
-      for (uint32_t i = threadIdx.x; i < n_cand; i += blockDim.x) {
-        uint32_t k = k_lo + i;
-        if (k >= K) k -= K;
-        const uint32_t y = (uint32_t)(((uint64_t)phi + 3ull * k + 2ull * L - base) % L);
-        if (y < lo || y + 2u >= hi) continue;
-        uint32_t a = smem[y], b = smem[y + 1u], c = smem[y + 2u];
-        const Masks m = rate_masks(k, n, g, P.k0, P.k1, P.T);
-        window_update(a, b, c, m);
-        smem[y] = a;
-        smem[y + 1u] = b;
-        smem[y + 2u] = c;
+      // window coordinate of tile position lo: w = (base + lo - phi) mod L; windows start at
+      // w = 3k (k < K); w in [3K, L) is idle
+      w_lo = base + G.lo + L - G.phi;
+      if (w_lo >= L) w_lo -= L;
+      if (w_lo >= L) w_lo -= L;
+      if (w_lo < 3u * K) {
+        G.k_lo = w_lo / 3u;
+        G.y_first = (int)G.lo - (int)(w_lo - 3u * G.k_lo);
+      } else {
+        G.k_lo = 0u;
+        G.y_first = (int)G.lo + (int)(L - w_lo);
       }
+      G.n_cand = (G.hi - G.lo) / 3u + 2u;
+    }
+
+    // ---- first pass: blocks 0-2 for every window; undecided windows are deferred ----
+    for (uint32_t i0 = warp * 32u; i0 < G.n_cand; i0 += blockDim.x) {
+      const uint32_t i = i0 + lane;
+      uint32_t k = 0, ia = 0, ib = 0, ic = 0;
+      const bool valid = candidate<RING>(G, i, L, K, k, ia, ib, ic);
+      Cmp cD = cmp_init(P.T.td, P.T.td_full), cA = cmp_init(P.T.tda, P.T.tda_full);
+      uint32_t O;
+      {
+        uint32_t x0 = k, x1 = n, x2 = g, x3 = kTagDyn << 28;
+        uint32_t y0 = k, y1 = n, y2 = g, y3 = (kTagDyn << 28) | 1u;
+        uint32_t z0 = k, z1 = n, z2 = g, z3 = (kTagDyn << 28) | 2u;
+        philox4x32_10_rk(x0, x1, x2, x3, P.rk);
+        philox4x32_10_rk(y0, y1, y2, y3, P.rk);
+        philox4x32_10_rk(z0, z1, z2, z3, P.rk);
+        O = x0;
+        const uint32_t w[11] = {x1, x2, x3, y0, y1, y2, y3, z0, z1, z2, z3};   // planes 31..21
+        cmp_group<11>(cD, w, P.T.tmD, 31);
+        cmp_group<11>(cA, w, P.T.tmA, 31);
+      }
+      const bool open = cmp_open2(cD, P.T.lo_d, 21) || cmp_open2(cA, P.T.lo_da, 21);
+      if (valid && !open) apply_window(smem, ia, ib, ic, O, cD.lt, cA.lt);
+      if (valid && open) {
+        const uint32_t p3 = atomicAdd(&s_q3n, 1u);
+        if (p3 < (uint32_t)kQ3Cap) {
+          q3[0 * kQ3Cap + p3] = i;
+          q3[1 * kQ3Cap + p3] = O;
+          q3[2 * kQ3Cap + p3] = cD.lt;
+          q3[3 * kQ3Cap + p3] = cD.eq;
+          q3[4 * kQ3Cap + p3] = cA.lt;
+          q3[5 * kQ3Cap + p3] = cA.eq;
+        } else {  // list full: finish here
+          finish_from3(k, n, g, P.rk, P.T, cD, cA);
+          apply_window(smem, ia, ib, ic, O, cD.lt, cA.lt);
+        }
+      }
+    }
+    __syncthreads();
+    // ---- second pass: blocks 3..8 for the few windows still open ----
+    const uint32_t nq3 = min(s_q3n, (uint32_t)kQ3Cap);
+    for (uint32_t e = threadIdx.x; e < nq3; e += blockDim.x) {
+      const uint32_t di = q3[0 * kQ3Cap + e];
+      const uint32_t dO = q3[1 * kQ3Cap + e];
+      Cmp dD, dA;
+      dD.lt = q3[2 * kQ3Cap + e];
+      dD.eq = q3[3 * kQ3Cap + e];
+      dA.lt = q3[4 * kQ3Cap + e];
+      dA.eq = q3[5 * kQ3Cap + e];
+      uint32_t dk = 0, da = 0, db = 0, dc = 0;
+      candidate<RING>(G, di, L, K, dk, da, db, dc);
+      finish_from3(dk, n, g, P.rk, P.T, dD, dA);
+      apply_window(smem, da, db, dc, dO, dD.lt, dA.lt);
+    }
+    if (!RING) {
       // shrink the valid region by the windows that straddle its edges
-      if (w_lo < 3u * K && (w_lo % 3u) != 0u) lo += 3u - (w_lo % 3u);
-      const uint32_t w_hi = (uint32_t)(((uint64_t)base + hi - 1u + L - phi) % L);
-      if (w_hi < 3u * K && (w_hi % 3u) != 2u) hi -= 1u + (w_hi % 3u);
+      const uint32_t lo_before = G.lo;
+      if (w_lo < 3u * K) {
+        const uint32_t rem = w_lo - 3u * G.k_lo;
+        if (rem) G.lo += 3u - rem;
+      }
+      uint32_t w_hi = w_lo + (G.hi - 1u - lo_before);
+      if (w_hi >= L) w_hi -= L;
+      if (w_hi < 3u * K) {
+        const uint32_t rem = w_hi % 3u;
+        if (rem != 2u) G.hi -= 1u + rem;
+      }
     }
     __syncthreads();
     if (r < P.n_rec && P.rec_sub[r] == n + 1u) {
@@ -349,32 +560,35 @@ __global__ void k_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t
   }
 }
 
-// Test entry: the MSB-first plane compare on explicit words (O, P31..P0) per item.
+// Test entry: the MSB-first plane compare on explicit words (O, P31..P0) per item, with
+// the grouping and exit rule of the sweep (planes 31..21 first, then blocks 3..8).
 __global__ void k_rate_masks(const uint32_t *words, Thresholds T, uint32_t *masks, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x) {
-    const uint32_t *w = words + 33 * i;
-    uint32_t ltD = T.td_full ? 0xFFFFFFFFu : 0u, gtD = (!T.td_full && T.td == 0u) ? 0xFFFFFFFFu : 0u;
-    uint32_t ltA = T.tda_full ? 0xFFFFFFFFu : 0u, gtA = (!T.tda_full && T.tda == 0u) ? 0xFFFFFFFFu : 0u;
-    // same block structure and exit rule as rate_masks, with the words read from memory
-    for (int b = 0; b <= 8; ++b) {
-      if (b > 0) {
-        const int m_prev = 33 - 4 * b;
-        if (!cmp_open(ltD, gtD, T.td, T.td_full, m_prev) &&
-            !cmp_open(ltA, gtA, T.tda, T.tda_full, m_prev))
-          break;
-      }
-      const int first = (b == 0) ? 31 : 32 - 4 * b;
-      const int cnt = (b == 0) ? 3 : (b < 8 ? 4 : 1);
-      for (int q = 0; q < cnt; ++q) {
-        const int m = first - q;
-        const uint32_t plane = w[32 - m];
-        if (!T.td_full) cmp_plane(ltD, gtD, plane, (T.td >> m) & 1u);
-        if (!T.tda_full) cmp_plane(ltA, gtA, plane, (T.tda >> m) & 1u);
+    const uint32_t *w = words + 33 * i;   // w[1 + q] = plane 31 - q
+    Cmp cD = cmp_init(T.td, T.td_full), cA = cmp_init(T.tda, T.tda_full);
+    {
+      const uint32_t g11[11] = {w[1], w[2], w[3], w[4], w[5], w[6], w[7], w[8], w[9], w[10], w[11]};
+      cmp_group<11>(cD, g11, T.tmD, 31);
+      cmp_group<11>(cA, g11, T.tmA, 31);
+    }
+#pragma unroll
+    for (int b = 3; b <= 8; ++b) {
+      const int m_prev = 33 - 4 * b;
+      if (!cmp_open2(cD, T.lo_d, m_prev) && !cmp_open2(cA, T.lo_da, m_prev)) break;
+      const int m0 = 32 - 4 * b;
+      if (b < 8) {
+        const uint32_t g[4] = {w[32 - m0], w[33 - m0], w[34 - m0], w[35 - m0]};
+        cmp_group<4>(cD, g, T.tmD, m0);
+        cmp_group<4>(cA, g, T.tmA, m0);
+      } else {
+        const uint32_t g[1] = {w[32]};
+        cmp_group<1>(cD, g, T.tmD, 0);
+        cmp_group<1>(cA, g, T.tmA, 0);
       }
     }
-    masks[3 * i] = ltD;
-    masks[3 * i + 1] = ltA & ~ltD;
+    masks[3 * i] = cD.lt;
+    masks[3 * i + 1] = cA.lt & ~cD.lt;
     masks[3 * i + 2] = w[0];
   }
 }
