@@ -9,7 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libpcpd.so")
 SOURCES = [os.path.join(CSRC, "pcpd_capi.cu")]
-DEPS = SOURCES + [os.path.join(CSRC, "pcpd_kernels.cuh"),
+DEPS = SOURCES + [os.path.join(CSRC, "pcpd_kernels.cuh"), os.path.join(CSRC, "pcpd_engine.cuh"),
                   os.path.join(os.path.dirname(HERE), "include", "pcpd.h")]
 
 

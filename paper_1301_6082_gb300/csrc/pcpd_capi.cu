@@ -11,7 +11,7 @@
 #include <vector>
 
 #include "../../include/pcpd.h"
-#include "pcpd_kernels.cuh"
+#include "pcpd_engine.cuh"
 
 namespace {
 
@@ -116,7 +116,7 @@ constexpr size_t kStaticSmem = sizeof(uint32_t) * pcpdk::kPhiChunk + 34 * sizeof
 
 // ------------------------------------------------------------------------------------------
 struct pcpd {
-  uint32_t L = 0, K = 0, S = 0, G = 0;
+  uint32_t L = 0, K = 0, S = 0, G = 0, pitch = 0;
   double p = 0, d = 0;
   uint64_t seed = 0, td = 0, tda = 0;
   pcpdk::Thresholds T{};
@@ -136,33 +136,55 @@ struct pcpd {
   size_t rec_cap = 0;
   uint32_t *d_rec_sub = nullptr;
   size_t rec_sub_cap = 0;
-  // plan
+  // plan (see make_plan)
   bool ring = true;
-  uint32_t threads = 0, core = 0, halo = 0, tau = 0, n_seg = 1;
-  size_t dyn_smem = 0;
+  uint32_t gpi = 1, threads = 0, core = 0, halo = 0, tau = 0, n_seg = 1;
+  size_t tile_words = 0, dyn_smem = 0;
+  int grid = 0;
+  // engine scratch: per-tile epoch flags, work counter, error word
+  uint32_t *d_done = nullptr;   // [tiles], then counter, then error word
+  uint32_t tiles = 0;
 };
 
 namespace {
 
+// Tile plan.  Columns that fit in shared memory run as RING tiles (whole columns, gpi of them
+// per CTA when they are short, so that a CTA has enough windows per sub-step); longer columns
+// are cut into equal SEGMENT tiles with a halo of 2*tau sites.  No plan changes a result bit.
 int make_plan(pcpd_t *h, const pcpd_params *prm) {
-  int optin = 0;
+  int optin = 0, dev = 0, sms = 0;
   int rc = smem_optin(&optin);
   if (rc) return rc;
-  const size_t avail_words = ((size_t)optin - kStaticSmem) / 4 - pcpdk::sweep_queue_words(32);
+  CU(cudaGetDevice(&dev));
+  CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const size_t list_words = pcpdk::sweep_queue_words(32);
+  const size_t avail_words = ((size_t)optin - kStaticSmem) / 4 - list_words;
   const uint32_t L = h->L;
   const uint32_t seg_override = prm ? prm->plan_seg_sites : 0;
+  h->tau = (prm && prm->plan_tau) ? prm->plan_tau : 128u;
+  if (h->tau == 0u) return fail(PCPD_EINVAL, "plan_tau must be positive");
   if (seg_override == 0 && L <= avail_words) {
     h->ring = true;
     h->core = L;
     h->halo = 0;
     h->n_seg = 1;
-    uint32_t want = (h->K + 31u) / 32u * 32u;
+    // columns per tile: up to 4 (one phase group), while they fit, the CTA lacks windows and
+    // there are still enough tiles to give every SM one
+    uint32_t gpi = 1;
+    while (gpi < 4 && h->G % (2 * gpi) == 0 && (size_t)(2 * gpi) * L <= avail_words && gpi * h->K < 4096 &&
+           h->G / (2 * gpi) >= (uint32_t)sms)
+      gpi *= 2;
+    h->gpi = gpi;
+    // a RING tile keeps its columns for a long stretch of sub-steps
+    h->tau = (prm && prm->plan_tau) ? prm->plan_tau : (1u << 20);
+    uint32_t want = (gpi * h->K + 31u) / 32u * 32u;
     if (want > 1024u) want = 1024u;
-    if (want < 32u) want = 32u;
+    if (want < 64u) want = 64u;
     h->threads = want;
+    h->tile_words = (size_t)gpi * L;
   } else {
     h->ring = false;
-    h->tau = (prm && prm->plan_tau) ? prm->plan_tau : 128u;
+    h->gpi = 1;
     h->halo = 2u * h->tau;
     uint32_t core;
     if (seg_override) {
@@ -172,24 +194,28 @@ int make_plan(pcpd_t *h, const pcpd_params *prm) {
       if (max_core < 1024) return fail(PCPD_EINVAL, "temporal block tau=%u too large for shared memory", h->tau);
       const uint32_t nseg = (uint32_t)((L + max_core - 1) / max_core);
       core = (L + nseg - 1) / nseg;
+      core = (core + 3u) & ~3u;   // keep tile starts 16-byte aligned
     }
     h->core = core;
     h->n_seg = (L + core - 1) / core;
-    const size_t tile = (size_t)core + 2u * h->halo;
-    if (tile > avail_words) return fail(PCPD_EINVAL, "tile of %zu sites exceeds shared memory", tile);
-    if (h->n_seg < 2 || tile + 12 > L)
+    h->tile_words = (size_t)core + 2u * h->halo;
+    if (h->tile_words > avail_words) return fail(PCPD_EINVAL, "tile of %zu sites exceeds shared memory", h->tile_words);
+    if (h->n_seg < 2 || h->tile_words + 12 > L)
       return fail(PCPD_EINVAL, "segmented plan needs >= 2 tiles each shorter than L-12 (L=%u, core=%u, halo=%u)", L, core, h->halo);
     h->threads = 1024;
   }
   if (prm && prm->plan_threads) {
-    if (prm->plan_threads % 32 || prm->plan_threads > 1024)
-      return fail(PCPD_EINVAL, "plan_threads must be a multiple of 32 and <= 1024");
+    if (prm->plan_threads % 32 || prm->plan_threads > 1024 || prm->plan_threads < 64)
+      return fail(PCPD_EINVAL, "plan_threads must be a multiple of 32 in [64, 1024]");
     h->threads = prm->plan_threads;
   }
-  const size_t tile_words = h->ring ? (size_t)L : (size_t)h->core + 2u * h->halo;
-  h->dyn_smem = 4 * (tile_words + pcpdk::sweep_queue_words((int)(h->threads / 32)));
-  if (h->dyn_smem + kStaticSmem > (size_t)optin)
-    return fail(PCPD_EINVAL, "tile of %zu sites plus queues exceeds shared memory", tile_words);
+  h->dyn_smem = 4 * (h->tile_words + list_words);
+  CU(cudaFuncSetAttribute(pcpdk::k_sweep_persistent<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->dyn_smem));
+  int per_sm = 0;
+  CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcpdk::k_sweep_persistent<false>, (int)h->threads, h->dyn_smem));
+  if (per_sm < 1) return fail(PCPD_EINVAL, "tile plan does not fit one CTA per SM");
+  h->grid = per_sm * sms;
+  h->tiles = (h->G / h->gpi) * h->n_seg;
   return PCPD_OK;
 }
 
@@ -232,57 +258,73 @@ int ensure_rec_sub(pcpd_t *h, size_t need) {
   return PCPD_OK;
 }
 
-// Launch the sweep from n_now to n_end; records rec_sub[0..n) (absolute sub-steps in
-// (n_now, n_end], device copy at d_sub) go to record slots [slot0, slot0+n).
+// The error word of the engine: 0, or a device-side wait that ran out of its budget.
+int check_engine(const pcpd_t *h) {
+  uint32_t err = 0;
+  CU(cudaMemcpyAsync(&err, h->d_done + h->tiles + 1, 4, cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  if (err) return fail(PCPD_ETIMEOUT, "device wait ran out of its budget (code %u)", err);
+  return PCPD_OK;
+}
+
+// Clock cycles an engine item may wait for another item or a copy before it gives up.
+constexpr unsigned long long kSpinLimit = 40ull * 1000 * 1000 * 1000;   // ~20 s at 2 GHz
+
+// Sweep from n_now to n_end in engine launches; records subs[0..) (absolute sub-steps in
+// (n_now, n_end], already copied to d_rec_sub) go to record slots [slot0, ...).
 int launch_sweep(pcpd_t *h, uint64_t n_end, const std::vector<uint64_t> &subs, size_t slot0) {
-  pcpdk::SweepParams P{};
-  P.L = h->L;
-  P.K = h->K;
-  P.G = h->G;
-  P.S = h->S;
-  P.k0 = h->k0;
-  P.k1 = h->k1;
-  P.rk = pcpdk::make_round_keys(h->k0, h->k1);
-  P.T = h->T;
-  P.core = h->core;
-  P.halo = h->halo;
-  const dim3 block(h->threads);
-  const dim3 grid(h->n_seg, h->G);
+  const uint64_t max_epochs = 1u << 22;
   size_t ri = 0;
-  if (h->ring) {
-    CU(cudaFuncSetAttribute(pcpdk::k_sweep_tile<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->dyn_smem));
-  } else {
-    CU(cudaFuncSetAttribute(pcpdk::k_sweep_tile<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->dyn_smem));
-  }
-  // RING: the whole range in launches of at most 2^20 sub-steps; SEGMENT: tau sub-steps each
-  const uint64_t chunk = h->ring ? (1ull << 20) : h->tau;
-  uint64_t n = h->n_now;
-  while (n < n_end) {
-    const uint64_t nb = (n_end - n > chunk) ? n + chunk : n_end;
+  while (h->n_now < n_end) {
+    const uint64_t span = n_end - h->n_now;
+    const uint64_t epochs_all = (span + h->tau - 1) / h->tau;
+    const uint64_t epochs = epochs_all > max_epochs ? max_epochs : epochs_all;
+    const uint64_t nb = (epochs == epochs_all) ? n_end : h->n_now + epochs * h->tau;
     size_t rj = ri;
     while (rj < subs.size() && subs[rj] <= nb) ++rj;
-    P.n_begin = (uint32_t)n;
-    P.n_end = (uint32_t)nb;
-    P.rec_sub = h->d_rec_sub + ri;
-    P.n_rec = (uint32_t)(rj - ri);
-    P.rec_total = h->d_rec_total ? h->d_rec_total + slot0 + ri : nullptr;
-    P.rec_sample = h->per_sample ? h->d_rec_sample + (slot0 + ri) * (size_t)h->S : nullptr;
-    if (h->ring) {
-      P.src = h->buf[h->cur];
-      P.dst = h->buf[h->cur];
-      pcpdk::k_sweep_tile<true><<<grid, block, h->dyn_smem, h->stream>>>(P);
-    } else {
-      P.src = h->buf[h->cur];
-      P.dst = h->buf[1 - h->cur];
-      pcpdk::k_sweep_tile<false><<<grid, block, h->dyn_smem, h->stream>>>(P);
-      h->cur = 1 - h->cur;
-    }
+    pcpdk::BatchParams B;
+    memset(&B, 0, sizeof B);
+    pcpdk::InstDesc &D = B.single;
+    D.L = h->L;
+    D.K = h->K;
+    D.G = h->G;
+    D.S = h->S;
+    D.pitch = h->pitch;
+    D.k0 = h->k0;
+    D.k1 = h->k1;
+    D.ring = h->ring ? 1u : 0u;
+    D.gpi = h->gpi;
+    D.core = h->core;
+    D.halo = h->halo;
+    D.tau = h->tau;
+    D.n_seg = h->n_seg;
+    D.n_begin = (uint32_t)h->n_now;
+    D.n_end = (uint32_t)nb;
+    D.n_rec = (uint32_t)(rj - ri);
+    D.buf0 = h->buf[h->cur];
+    D.buf1 = h->buf[1 - h->cur];
+    D.rec_sub = h->d_rec_sub + ri;
+    D.rec_total = h->d_rec_total ? h->d_rec_total + slot0 + ri : nullptr;
+    D.rec_sample = h->per_sample ? h->d_rec_sample + (slot0 + ri) * (size_t)h->S : nullptr;
+    D.done = h->d_done;
+    D.rk = pcpdk::make_round_keys(h->k0, h->k1);
+    D.T = h->T;
+    CU(cudaMemsetAsync(h->d_done, 0, (h->tiles + 1) * sizeof(uint32_t), h->stream));  // flags + counter
+    B.items = nullptr;
+    B.n_items = (uint32_t)(epochs * h->tiles);
+    B.tiles_per_epoch = h->tiles;
+    B.counter = h->d_done + h->tiles;
+    B.err = h->d_done + h->tiles + 1;
+    B.tile_words = (uint32_t)h->tile_words;
+    B.spin_limit = kSpinLimit;
+    const int grid = (int)((uint64_t)h->grid < B.n_items ? (uint64_t)h->grid : B.n_items);
+    pcpdk::k_sweep_persistent<false><<<grid, h->threads, h->dyn_smem, h->stream>>>(B);
     CU(cudaGetLastError());
     g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (epochs & 1u) h->cur = 1 - h->cur;
+    h->n_now = nb;
     ri = rj;
-    n = nb;
   }
-  h->n_now = n_end;
   return PCPD_OK;
 }
 
@@ -342,10 +384,12 @@ int pcpd_create_ex(const pcpd_params *prm, pcpd_t **out) {
     if (e != cudaSuccess) return bail(fail(PCPD_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e)));
     h->own_stream = true;
   }
-  const size_t words = (size_t)h->G * h->L;
+  // device rows are padded to a multiple of 4 words so that tiles can move by TMA
+  h->pitch = (h->L + 3u) & ~3u;
+  const size_t words = (size_t)h->G * h->pitch;
   if (prm->dev_lattice) {
     if (prm->dev_bytes < 2 * words * 4 || ((uintptr_t)prm->dev_lattice & 255u))
-      return bail(fail(PCPD_EINVAL, "dev_lattice must be 256-byte aligned and hold 2*G*L words (%zu bytes)", 2 * words * 4));
+      return bail(fail(PCPD_EINVAL, "dev_lattice must be 256-byte aligned and hold 2*G*ceil4(L) words (%zu bytes)", 2 * words * 4));
     h->buf[0] = (uint32_t *)prm->dev_lattice;
     h->buf[1] = h->buf[0] + words;
   } else {
@@ -354,7 +398,12 @@ int pcpd_create_ex(const pcpd_params *prm, pcpd_t **out) {
     h->buf[1] = h->buf[0] + words;
     h->own_mem = true;
   }
-  pcpdk::k_init<<<1024, 256, 0, h->stream>>>(h->buf[0], h->L, h->G, h->init, h->k0, h->k1);
+  {
+    cudaError_t e = cudaMalloc(&h->d_done, (h->tiles + 2) * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_done, 0, (h->tiles + 2) * sizeof(uint32_t), h->stream);
+    if (e != cudaSuccess) return bail(fail(PCPD_ENOMEM, "engine scratch: %s", cudaGetErrorString(e)));
+  }
+  pcpdk::k_init<<<1024, 256, 0, h->stream>>>(h->buf[0], h->L, h->pitch, h->G, h->init, h->k0, h->k1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return bail(fail(PCPD_ECUDA, "init launch: %s", cudaGetErrorString(e)));
   g_launches.fetch_add(1, std::memory_order_relaxed);
@@ -378,6 +427,7 @@ void pcpd_destroy(pcpd_t *h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->own_mem) cudaFree(h->buf[0]);
+  cudaFree(h->d_done);
   cudaFree(h->d_rec_total);
   cudaFree(h->d_rec_sample);
   cudaFree(h->d_rec_sub);
@@ -411,7 +461,7 @@ int pcpd_run(pcpd_t *h, uint64_t steps_mcs, const uint64_t *times, size_t n_time
   if (rc) return rc;
   size_t slot = slot0;
   if (now_first) {
-    pcpdk::k_count<<<h->G, 256, 0, h->stream>>>(h->buf[h->cur], h->L, h->S, h->d_rec_total + slot,
+    pcpdk::k_count<<<h->G, 256, 0, h->stream>>>(h->buf[h->cur], h->L, h->pitch, h->S, h->d_rec_total + slot,
                                                  h->per_sample ? h->d_rec_sample + slot * (size_t)h->S : nullptr);
     CU(cudaGetLastError());
     g_launches.fetch_add(1, std::memory_order_relaxed);
@@ -450,7 +500,7 @@ uint64_t pcpd_time_mcs(const pcpd_t *h) { return h ? h->t_now : 0; }
 int pcpd_sync(pcpd_t *h) {
   if (!h) return fail(PCPD_EINVAL, "NULL handle");
   CU(cudaStreamSynchronize(h->stream));
-  return PCPD_OK;
+  return check_engine(h);
 }
 
 int pcpd_density(const pcpd_t *h, double *rho_out, uint64_t *counts_out, size_t n) {
@@ -460,6 +510,8 @@ int pcpd_density(const pcpd_t *h, double *rho_out, uint64_t *counts_out, size_t 
   std::vector<unsigned long long> c(n);
   CU(cudaMemcpyAsync(c.data(), h->d_rec_total, n * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));
   CU(cudaStreamSynchronize(h->stream));
+  int rc = check_engine(h);
+  if (rc) return rc;
   const double denom = (double)h->L * (double)h->S;
   for (size_t i = 0; i < n; ++i) {
     if (counts_out) counts_out[i] = c[i];
@@ -486,15 +538,17 @@ int pcpd_sample_counts(const pcpd_t *h, size_t r, uint32_t *out) {
 
 int pcpd_get_lattice(const pcpd_t *h, uint32_t *host_out) {
   if (!h || !host_out) return fail(PCPD_EINVAL, "NULL argument");
-  CU(cudaMemcpyAsync(host_out, h->buf[h->cur], (size_t)h->G * h->L * 4, cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaMemcpy2DAsync(host_out, (size_t)h->L * 4, h->buf[h->cur], (size_t)h->pitch * 4, (size_t)h->L * 4, h->G,
+                       cudaMemcpyDeviceToHost, h->stream));
   CU(cudaStreamSynchronize(h->stream));
-  return PCPD_OK;
+  return check_engine(h);
 }
 
 int pcpd_set_lattice(pcpd_t *h, const uint32_t *host_in, uint64_t substep) {
   if (!h || !host_in) return fail(PCPD_EINVAL, "NULL argument");
   if (substep > 0xFFFFFFFFull) return fail(PCPD_EINVAL, "sub-step must be < 2^32");
-  CU(cudaMemcpyAsync(h->buf[h->cur], host_in, (size_t)h->G * h->L * 4, cudaMemcpyHostToDevice, h->stream));
+  CU(cudaMemcpy2DAsync(h->buf[h->cur], (size_t)h->pitch * 4, host_in, (size_t)h->L * 4, (size_t)h->L * 4, h->G,
+                       cudaMemcpyHostToDevice, h->stream));
   CU(cudaStreamSynchronize(h->stream));
   h->n_now = substep;
   h->t_now = time_of_substep(h->L, substep);

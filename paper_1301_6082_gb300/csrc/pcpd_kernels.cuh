@@ -217,41 +217,26 @@ __device__ __forceinline__ uint32_t phase_of(uint32_t n, uint32_t h, uint32_t L,
 }
 
 // ---------------------------------------------------------------------------------------
-// Tile sweep.  One CTA owns a tile of one 32-sample group's column in shared memory:
-//  RING: the whole column (tile = L sites, periodic indexing);
-//  SEGMENT: core sites [s0, s0+core) plus a halo of H sites on each side (temporal
-//  blocking): the windows of each sub-step are computed wherever all three sites are still
-//  valid, and the valid region shrinks by at most 2 sites per side per sub-step, so after
-//  tau <= H/2 sub-steps the core is exact.  Windows inside the halo are recomputed
+// Tiles.  A CTA owns a tile of 32-sample group columns in shared memory:
+//  RING: whole columns (tile = L sites each, periodic indexing);
+//  SEGMENT: core sites [s0, s0+core) of one column plus a halo of H sites on each side
+//  (temporal blocking): the windows of each sub-step are computed wherever all three sites
+//  are still valid, and the valid region shrinks by at most 2 sites per side per sub-step,
+//  so after tau <= H/2 sub-steps the core is exact.  Windows inside the halo are recomputed
 //  redundantly; counter-based random numbers make the recomputation identical.
 // ---------------------------------------------------------------------------------------
-struct SweepParams {
-  const uint32_t *src;          // lattice [G][L] before the sub-steps
-  uint32_t *dst;                // lattice [G][L] after (may equal src in RING mode)
-  uint32_t L, K, G, S;
-  uint32_t core;                // core sites per tile (RING: L)
-  uint32_t halo;                // H (RING: 0)
-  uint32_t k0, k1;              // Philox key
-  RoundKeys rk;                 // its round keys
-  Thresholds T;
-  uint32_t n_begin, n_end;      // sub-steps [n_begin, n_end)
-  const uint32_t *rec_sub;      // records: state after rec_sub[r] sub-steps, in (n_begin, n_end]
-  uint32_t n_rec;
-  unsigned long long *rec_total;  // [n_rec] += occupied pairs
-  uint32_t *rec_sample;           // [n_rec][S] += per-sample counts, or nullptr
-};
-
 constexpr int kPhiChunk = 256;
 
-// Count occupied sites of tile words [y0, y1) into record r.
+// Count occupied sites of tile words [y0, y1) of group g into record r: the total into
+// rec_total[r] and, if rec_sample is set, sample 32g+j's count into rec_sample[r*S + 32g + j].
 __device__ __forceinline__ void tile_count(const uint32_t *sm, uint32_t y0, uint32_t y1,
-                                           const SweepParams &P, uint32_t r, uint32_t g,
-                                           unsigned int *s_red) {
+                                           unsigned long long *rec_total, uint32_t *rec_sample,
+                                           uint32_t S, uint32_t r, uint32_t g, unsigned int *s_red) {
   unsigned int local = 0;
   for (uint32_t y = y0 + threadIdx.x; y < y1; y += blockDim.x) local += __popc(sm[y]);
   local = __reduce_add_sync(0xFFFFFFFFu, local);
   if ((threadIdx.x & 31) == 0) atomicAdd(&s_red[32], local);
-  if (P.rec_sample) {
+  if (rec_sample) {
     unsigned int cnt[32];
 #pragma unroll
     for (int j = 0; j < 32; ++j) cnt[j] = 0;
@@ -267,9 +252,9 @@ __device__ __forceinline__ void tile_count(const uint32_t *sm, uint32_t y0, uint
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0) atomicAdd(&P.rec_total[r], (unsigned long long)s_red[32]);
-  if (P.rec_sample && threadIdx.x < 32)
-    atomicAdd(&P.rec_sample[(size_t)r * P.S + 32u * g + threadIdx.x], s_red[threadIdx.x]);
+  if (threadIdx.x == 0) atomicAdd(&rec_total[r], (unsigned long long)s_red[32]);
+  if (rec_sample && threadIdx.x < 32)
+    atomicAdd(&rec_sample[(size_t)r * S + 32u * g + threadIdx.x], s_red[threadIdx.x]);
   __syncthreads();
   for (uint32_t t = threadIdx.x; t <= 32u; t += blockDim.x) s_red[t] = 0;
   __syncthreads();
@@ -360,170 +345,31 @@ __device__ __forceinline__ void apply_window(uint32_t *sm, uint32_t ia, uint32_t
   sm[ic] = c;
 }
 
-template <bool RING>
-__global__ void __launch_bounds__(1024, 1) k_sweep_tile(const SweepParams P) {
-  extern __shared__ __align__(16) uint32_t smem[];
-  __shared__ uint32_t s_phi[kPhiChunk];
-  __shared__ unsigned int s_red[33];
-  __shared__ unsigned int s_q3n;
-
-  const uint32_t g = blockIdx.y;
-  const uint32_t L = P.L, K = P.K;
-  const uint32_t s0 = RING ? 0u : blockIdx.x * P.core;
-  const uint32_t core_len = RING ? L : min(P.core, L - s0);
-  const uint32_t H = RING ? 0u : P.halo;
-  const uint32_t tile_len = core_len + 2u * H;
-  const uint32_t base = RING ? 0u : (uint32_t)(((uint64_t)s0 + L - H) % L);
-  const uint32_t h = (32u * g) / 128u;
-  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-
-  // the deferred-window list follows the tile words: Q3[field][kQ3Cap]
-  const uint32_t tile_words = RING ? L : P.core + 2u * P.halo;
-  uint32_t *q3 = smem + tile_words;
-
-  const uint32_t *src = P.src + (size_t)g * L;
-  for (uint32_t y = threadIdx.x; y < tile_len; y += blockDim.x) {
-    uint32_t x = base + y;
-    if (x >= L) x -= L;
-    smem[y] = src[x];
-  }
-  for (uint32_t t = threadIdx.x; t <= 32u; t += blockDim.x) s_red[t] = 0;
-  __syncthreads();
-
-  Geometry G;
-  G.lo = 0;
-  G.hi = tile_len;
-  G.gap = L - 3u * K;
-  uint32_t r = 0;  // next record
-  for (uint32_t n = P.n_begin; n < P.n_end; ++n) {
-    const uint32_t j = (n - P.n_begin) % kPhiChunk;
-    if (j == 0) {
-      for (uint32_t t = threadIdx.x; t < kPhiChunk; t += blockDim.x)
-        s_phi[t] = phase_of(n + t, h, L, P.k0, P.k1);
-    }
-    if (threadIdx.x == 0) s_q3n = 0;
-    __syncthreads();
-    G.phi = s_phi[j];
-    uint32_t w_lo = 0;
-    if (RING) {
-      G.n_cand = K;
-    } else {
-      // window coordinate of tile position lo: w = (base + lo - phi) mod L; windows start at
-      // w = 3k (k < K); w in [3K, L) is idle
-      w_lo = base + G.lo + L - G.phi;
-      if (w_lo >= L) w_lo -= L;
-      if (w_lo >= L) w_lo -= L;
-      if (w_lo < 3u * K) {
-        G.k_lo = w_lo / 3u;
-        G.y_first = (int)G.lo - (int)(w_lo - 3u * G.k_lo);
-      } else {
-        G.k_lo = 0u;
-        G.y_first = (int)G.lo + (int)(L - w_lo);
-      }
-      G.n_cand = (G.hi - G.lo) / 3u + 2u;
-    }
-
-    // ---- first pass: blocks 0-2 for every window; undecided windows are deferred ----
-    for (uint32_t i0 = warp * 32u; i0 < G.n_cand; i0 += blockDim.x) {
-      const uint32_t i = i0 + lane;
-      uint32_t k = 0, ia = 0, ib = 0, ic = 0;
-      const bool valid = candidate<RING>(G, i, L, K, k, ia, ib, ic);
-      Cmp cD = cmp_init(P.T.td, P.T.td_full), cA = cmp_init(P.T.tda, P.T.tda_full);
-      uint32_t O;
-      {
-        uint32_t x0 = k, x1 = n, x2 = g, x3 = kTagDyn << 28;
-        uint32_t y0 = k, y1 = n, y2 = g, y3 = (kTagDyn << 28) | 1u;
-        uint32_t z0 = k, z1 = n, z2 = g, z3 = (kTagDyn << 28) | 2u;
-        philox4x32_10_rk(x0, x1, x2, x3, P.rk);
-        philox4x32_10_rk(y0, y1, y2, y3, P.rk);
-        philox4x32_10_rk(z0, z1, z2, z3, P.rk);
-        O = x0;
-        const uint32_t w[11] = {x1, x2, x3, y0, y1, y2, y3, z0, z1, z2, z3};   // planes 31..21
-        cmp_group<11>(cD, w, P.T.tmD, 31);
-        cmp_group<11>(cA, w, P.T.tmA, 31);
-      }
-      const bool open = cmp_open2(cD, P.T.lo_d, 21) || cmp_open2(cA, P.T.lo_da, 21);
-      if (valid && !open) apply_window(smem, ia, ib, ic, O, cD.lt, cA.lt);
-      if (valid && open) {
-        const uint32_t p3 = atomicAdd(&s_q3n, 1u);
-        if (p3 < (uint32_t)kQ3Cap) {
-          q3[0 * kQ3Cap + p3] = i;
-          q3[1 * kQ3Cap + p3] = O;
-          q3[2 * kQ3Cap + p3] = cD.lt;
-          q3[3 * kQ3Cap + p3] = cD.eq;
-          q3[4 * kQ3Cap + p3] = cA.lt;
-          q3[5 * kQ3Cap + p3] = cA.eq;
-        } else {  // list full: finish here
-          finish_from3(k, n, g, P.rk, P.T, cD, cA);
-          apply_window(smem, ia, ib, ic, O, cD.lt, cA.lt);
-        }
-      }
-    }
-    __syncthreads();
-    // ---- second pass: blocks 3..8 for the few windows still open ----
-    const uint32_t nq3 = min(s_q3n, (uint32_t)kQ3Cap);
-    for (uint32_t e = threadIdx.x; e < nq3; e += blockDim.x) {
-      const uint32_t di = q3[0 * kQ3Cap + e];
-      const uint32_t dO = q3[1 * kQ3Cap + e];
-      Cmp dD, dA;
-      dD.lt = q3[2 * kQ3Cap + e];
-      dD.eq = q3[3 * kQ3Cap + e];
-      dA.lt = q3[4 * kQ3Cap + e];
-      dA.eq = q3[5 * kQ3Cap + e];
-      uint32_t dk = 0, da = 0, db = 0, dc = 0;
-      candidate<RING>(G, di, L, K, dk, da, db, dc);
-      finish_from3(dk, n, g, P.rk, P.T, dD, dA);
-      apply_window(smem, da, db, dc, dO, dD.lt, dA.lt);
-    }
-    if (!RING) {
-      // shrink the valid region by the windows that straddle its edges
-      const uint32_t lo_before = G.lo;
-      if (w_lo < 3u * K) {
-        const uint32_t rem = w_lo - 3u * G.k_lo;
-        if (rem) G.lo += 3u - rem;
-      }
-      uint32_t w_hi = w_lo + (G.hi - 1u - lo_before);
-      if (w_hi >= L) w_hi -= L;
-      if (w_hi < 3u * K) {
-        const uint32_t rem = w_hi % 3u;
-        if (rem != 2u) G.hi -= 1u + rem;
-      }
-    }
-    __syncthreads();
-    if (r < P.n_rec && P.rec_sub[r] == n + 1u) {
-      tile_count(smem, H, H + core_len, P, r, g, s_red);
-      ++r;
-    }
-  }
-
-  uint32_t *dst = P.dst + (size_t)g * L;
-  for (uint32_t i = threadIdx.x; i < core_len; i += blockDim.x) dst[s0 + i] = smem[H + i];
-}
-
 // Initial lattice: mode 0 full, 1 empty, 2 i.i.d. Bernoulli(1/2) bits (Philox tag INIT,
 // counter (i, 0, g, INIT<<28), first word).
-__global__ void k_init(uint32_t *lat, uint32_t L, uint32_t G, int mode, uint32_t k0, uint32_t k1) {
+__global__ void k_init(uint32_t *lat, uint32_t L, uint32_t pitch, uint32_t G, int mode, uint32_t k0,
+                       uint32_t k1) {
   const size_t total = (size_t)G * L;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
        idx += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t g = (uint32_t)(idx / L), i = (uint32_t)(idx % L);
     uint32_t v;
     if (mode == 0) v = 0xFFFFFFFFu;
     else if (mode == 1) v = 0u;
     else {
-      const uint32_t g = (uint32_t)(idx / L), i = (uint32_t)(idx % L);
       uint32_t x0 = i, x1 = 0u, x2 = g, x3 = kTagInit << 28;
       philox4x32_10(x0, x1, x2, x3, k0, k1);
       v = x0;
     }
-    lat[idx] = v;
+    lat[(size_t)g * pitch + i] = v;
   }
 }
 
 // Record of the current state (no sub-step): one CTA per group.
-__global__ void k_count(const uint32_t *lat, uint32_t L, uint32_t S,
+__global__ void k_count(const uint32_t *lat, uint32_t L, uint32_t pitch, uint32_t S,
                         unsigned long long *rec_total, uint32_t *rec_sample) {
   const uint32_t g = blockIdx.x;
-  const uint32_t *col = lat + (size_t)g * L;
+  const uint32_t *col = lat + (size_t)g * pitch;
   unsigned int local = 0;
   unsigned int cnt[32];
 #pragma unroll
