@@ -150,6 +150,32 @@ int pcpd_dev_philox(const uint32_t *ctr, uint64_t seed, uint32_t *out, size_t n,
 int pcpd_dev_rate_masks(const uint32_t *words, uint64_t t_d, uint64_t t_da, uint32_t *masks,
                         size_t n, void *stream);
 
+/* ---- allocation-free sweep ----
+ * Advance a caller-owned lattice by n_substeps sub-steps without allocating any memory.
+ * The paper has no counterpart: this is an entry point for callers that cannot let a
+ * library allocate -- a host application whose device memory is all owned by its own pool
+ * or arena, or a latency-critical loop that cannot afford cudaMalloc/cudaFree, which can
+ * synchronize the whole device and can fail on a fragmented heap.  The caller passes the
+ * lattice in and out; the library's scratch (one epoch flag per tile, a work counter and an
+ * error word) is a fixed array of 16384 + 64 words inside the library, present on every GPU
+ * that loads it until the process exits.
+ *   lat_in   device, canonical layout [samples/32][L] uint32, 4-byte aligned: the state after
+ *            substep_begin sub-steps.  It is also used as work space: its contents are
+ *            undefined afterwards.
+ *   lat_out  device, same layout, not overlapping lat_in: receives the state after
+ *            substep_begin + n_substeps sub-steps (bit-identical to pcpd_run_substeps).
+ *   L, samples, p, d, seed   as for pcpd_create; stream: cudaStream_t or NULL.
+ * The call waits for the work to finish.  Errors: PCPD_EINVAL (bad sizes or pointers, or more
+ * tiles per epoch than the scratch holds -- about 16384 columns of up to ~50k sites, fewer
+ * for longer columns), PCPD_ENODEV, PCPD_ECUDA, PCPD_ETIMEOUT.
+ * Every call shares the one scratch array and clears it first; calls that overlap on the GPU
+ * (from several threads or streams at once) race on it and must not be made.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress); make that first
+ * call before any stream capture. */
+int pcpd_sweep_noalloc(uint32_t *lat_in, uint32_t *lat_out, uint32_t L, uint32_t samples, double p,
+                       double d, uint64_t seed, uint64_t substep_begin, uint64_t n_substeps,
+                       void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -585,3 +586,136 @@ int pcpd_dev_rate_masks(const uint32_t *words, uint64_t t_d, uint64_t t_da, uint
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------------
+// Allocation-free sweep (pcpd_sweep_noalloc).  Its scratch -- per-tile epoch flags, the work
+// counter and the error word -- lives in this fixed device array instead of memory the
+// library allocates.  The array exists on every device that loads the library, until exit.
+// ------------------------------------------------------------------------------------------
+namespace {
+
+constexpr uint32_t kNoAllocMaxTiles = 16384;   // tiles per epoch the array can serve
+constexpr size_t kNoAllocScratchWords = kNoAllocMaxTiles + 64;
+static __device__ __align__(256) uint32_t g_noalloc_scratch[kNoAllocScratchWords];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+uint32_t *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device (looked up once per device).
+int noalloc_scratch(uint32_t **out) {
+  int dev = 0;
+  CU(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(PCPD_ENODEV, "device index %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(PCPD_ECUDA, "cudaGetSymbolAddress(scratch) on device %d: %s", dev, cudaGetErrorString(e));
+    g_noalloc_ptr[dev] = (uint32_t *)p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return PCPD_OK;
+}
+
+}  // namespace
+
+extern "C" int pcpd_sweep_noalloc(uint32_t *lat_in, uint32_t *lat_out, uint32_t L, uint32_t samples,
+                                  double p, double d, uint64_t seed, uint64_t substep_begin,
+                                  uint64_t n_substeps, void *stream) {
+  if (!lat_in || !lat_out || lat_in == lat_out) return fail(PCPD_EINVAL, "need two distinct device lattices");
+  if (L < 3 || L >= (1u << 30)) return fail(PCPD_EINVAL, "L must satisfy 3 <= L < 2^30 (L=%u)", L);
+  if (samples == 0 || samples % 32 || samples > (1u << 22))
+    return fail(PCPD_EINVAL, "samples must be a positive multiple of 32, at most 2^22 (samples=%u)", samples);
+  if (substep_begin + n_substeps > 0xFFFFFFFFull || substep_begin + n_substeps < substep_begin)
+    return fail(PCPD_EINVAL, "sub-step count would reach 2^32");
+  uint64_t td, tda;
+  int rc = thresholds(p, d, &td, &tda);
+  if (rc) return rc;
+  rc = device_check();
+  if (rc) return rc;
+  pcpd h;   // plan only: no device memory is attached to it
+  h.L = L;
+  h.K = L / 3u;
+  h.S = samples;
+  h.G = samples / 32u;
+  h.pitch = L;
+  h.T = split_thresholds(td, tda);
+  h.k0 = (uint32_t)(seed & 0xFFFFFFFFu);
+  h.k1 = (uint32_t)(seed >> 32);
+  rc = make_plan(&h, nullptr);
+  if (rc) return rc;
+  if (h.tiles > kNoAllocMaxTiles)
+    return fail(PCPD_EINVAL, "%u tiles per epoch exceed the %u the allocation-free scratch holds (L=%u, samples=%u)",
+                h.tiles, kNoAllocMaxTiles, L, samples);
+  const size_t bytes = (size_t)(samples / 32u) * L * 4u;
+  if ((((uintptr_t)lat_in | (uintptr_t)lat_out) & 3u) != 0u)
+    return fail(PCPD_EINVAL, "lattice pointers must be 4-byte aligned");
+  if ((const char *)lat_in < (const char *)lat_out + bytes && (const char *)lat_out < (const char *)lat_in + bytes)
+    return fail(PCPD_EINVAL, "lat_in and lat_out overlap");
+  uint32_t *scratch = nullptr;
+  rc = noalloc_scratch(&scratch);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+
+  uint32_t *bufs[2] = {lat_in, lat_out};
+  int cur = 0;
+  uint64_t n_now = substep_begin;
+  const uint64_t n_end = substep_begin + n_substeps;
+  const uint64_t max_epochs = 1u << 22;
+  while (n_now < n_end) {
+    const uint64_t span = n_end - n_now;
+    const uint64_t epochs_all = (span + h.tau - 1) / h.tau;
+    const uint64_t epochs = epochs_all > max_epochs ? max_epochs : epochs_all;
+    const uint64_t nb = (epochs == epochs_all) ? n_end : n_now + epochs * h.tau;
+    pcpdk::BatchParams B;
+    memset(&B, 0, sizeof B);
+    pcpdk::InstDesc &D = B.single;
+    D.L = L;
+    D.K = h.K;
+    D.G = h.G;
+    D.S = samples;
+    D.pitch = L;
+    D.k0 = h.k0;
+    D.k1 = h.k1;
+    D.ring = h.ring ? 1u : 0u;
+    D.gpi = h.gpi;
+    D.core = h.core;
+    D.halo = h.halo;
+    D.tau = h.tau;
+    D.n_seg = h.n_seg;
+    D.n_begin = (uint32_t)n_now;
+    D.n_end = (uint32_t)nb;
+    D.buf0 = bufs[cur];
+    D.buf1 = bufs[1 - cur];
+    D.done = scratch;
+    D.rk = pcpdk::make_round_keys(h.k0, h.k1);
+    D.T = h.T;
+    // every call starts from cleared flags, counter and error word
+    CU(cudaMemsetAsync(scratch, 0, (h.tiles + 2) * sizeof(uint32_t), s));
+    B.items = nullptr;
+    B.n_items = (uint32_t)(epochs * h.tiles);
+    B.tiles_per_epoch = h.tiles;
+    B.counter = scratch + h.tiles;
+    B.err = scratch + h.tiles + 1;
+    B.tile_words = (uint32_t)h.tile_words;
+    B.spin_limit = kSpinLimit;
+    const int grid = (int)((uint64_t)h.grid < B.n_items ? (uint64_t)h.grid : B.n_items);
+    pcpdk::k_sweep_persistent<false><<<grid, h.threads, h.dyn_smem, s>>>(B);
+    CU(cudaGetLastError());
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    uint32_t err = 0;
+    CU(cudaMemcpyAsync(&err, scratch + h.tiles + 1, 4, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (err) return fail(PCPD_ETIMEOUT, "device wait ran out of its budget (code %u)", err);
+    if (epochs & 1u) cur = 1 - cur;
+    n_now = nb;
+  }
+  // the result must end in lat_out
+  if (cur == 0) {
+    CU(cudaMemcpyAsync(lat_out, lat_in, bytes, cudaMemcpyDeviceToDevice, s));
+    CU(cudaStreamSynchronize(s));
+  }
+  return PCPD_OK;
+}

@@ -57,6 +57,8 @@ SIGNATURES = [
     ("pcpd_substep_of_time", C.c_uint64, [C.c_uint32, C.c_uint64]),
     ("pcpd_dev_philox", C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_size_t, C.c_void_p]),
     ("pcpd_dev_rate_masks", C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_void_p, C.c_size_t, C.c_void_p]),
+    ("pcpd_sweep_noalloc", C.c_int, [C.c_void_p, C.c_void_p, C.c_uint32, C.c_uint32, C.c_double, C.c_double,
+                                     C.c_uint64, C.c_uint64, C.c_uint64, C.c_void_p]),
 ]
 
 _lib = None
@@ -210,3 +212,13 @@ def dev_rate_masks(words_dev, t_d: int, t_da: int, masks_dev, n: int, stream=Non
     s = C.c_void_p(int(getattr(stream, "cuda_stream", 0) or 0)) if stream is not None else None
     _check(load().pcpd_dev_rate_masks(C.c_void_p(words_dev.data_ptr()), t_d, t_da,
                                       C.c_void_p(masks_dev.data_ptr()), n, s))
+
+
+def sweep_noalloc(lat_in_dev, lat_out_dev, L: int, samples: int, p: float, d: float, seed: int,
+                  substep_begin: int, n_substeps: int, stream=None):
+    """Allocation-free sweep on caller-owned device lattices (torch CUDA tensors or objects
+    with data_ptr()): lat_out receives the state after n_substeps more sub-steps; lat_in is
+    used as work space.  For callers that cannot let the library allocate device memory."""
+    s = C.c_void_p(int(getattr(stream, "cuda_stream", 0) or 0)) if stream is not None else None
+    _check(load().pcpd_sweep_noalloc(C.c_void_p(lat_in_dev.data_ptr()), C.c_void_p(lat_out_dev.data_ptr()),
+                                     L, samples, p, d, seed, substep_begin, n_substeps, s))
