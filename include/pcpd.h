@@ -150,6 +150,40 @@ int pcpd_dev_philox(const uint32_t *ctr, uint64_t seed, uint32_t *out, size_t n,
 int pcpd_dev_rate_masks(const uint32_t *words, uint64_t t_d, uint64_t t_da, uint32_t *masks,
                         size_t n, void *stream);
 
+/* ---- batched heterogeneous instances in one persistent launch ----
+ * Independent systems run side by side, each with its own seed (the paper runs one system
+ * per workgroup, Sec. 3); here any number of instances with different L, samples, p, d,
+ * seeds, step counts and record times share one launch of the sweep engine through a
+ * device work queue.  Results are bit-identical to running each instance alone. */
+typedef struct pcpd_batch pcpd_batch_t;
+
+/* Create an empty batch whose work runs on `stream` (cudaStream_t; NULL = its own). */
+int pcpd_batch_create(void *stream, pcpd_batch_t **out);
+
+/* Add an instance (pcpd_params as for pcpd_create_ex; its stream and dev_lattice fields are
+ * ignored) to run for steps_mcs MCS from its initial state, with records at
+ * record_times_mcs[0..n_times) (strictly increasing, in (0, steps_mcs]; copied).  Device
+ * memory for the instance is allocated here.  *index_out (nullable) receives its index. */
+int pcpd_batch_add(pcpd_batch_t *b, const pcpd_params *prm, uint64_t steps_mcs,
+                   const uint64_t *record_times_mcs, size_t n_times, size_t *index_out);
+
+/* Run every instance to its end: one persistent launch per 128 instances (the launches run
+ * one after another; one batch may run at a time per process).  Waits for completion.
+ * Errors: PCPD_EINVAL, PCPD_ESTATE (ran already), PCPD_ECUDA, PCPD_ETIMEOUT. */
+int pcpd_batch_run(pcpd_batch_t *b);
+
+/* Number of instances added. */
+size_t pcpd_batch_size(const pcpd_batch_t *b);
+
+/* Record counts of instance i (occupied (site, sample) pairs, n <= its n_times). */
+int pcpd_batch_counts(const pcpd_batch_t *b, size_t i, uint64_t *counts_out, size_t n);
+
+/* Final lattice of instance i, canonical layout (G*L words).  Waits. */
+int pcpd_batch_lattice(const pcpd_batch_t *b, size_t i, uint32_t *host_out);
+
+/* Release the batch and all its instances.  NULL-safe. */
+void pcpd_batch_destroy(pcpd_batch_t *b);
+
 /* ---- allocation-free sweep ----
  * Advance a caller-owned lattice by n_substeps sub-steps without allocating any memory.
  * The paper has no counterpart: this is an entry point for callers that cannot let a

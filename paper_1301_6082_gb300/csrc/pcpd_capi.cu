@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -257,6 +258,36 @@ int ensure_rec_sub(pcpd_t *h, size_t need) {
   CU(cudaMalloc(&h->d_rec_sub, cap * sizeof(uint32_t)));
   h->rec_sub_cap = cap;
   return PCPD_OK;
+}
+
+// Descriptor of handle h for sub-steps [n_begin, n_end), records subs[ri..rj) in slots from slot.
+void fill_desc(const pcpd_t *h, pcpdk::InstDesc &D, uint64_t n_begin, uint64_t n_end, size_t ri, size_t rj,
+               size_t slot) {
+  memset(&D, 0, sizeof D);
+  D.L = h->L;
+  D.K = h->K;
+  D.G = h->G;
+  D.S = h->S;
+  D.pitch = h->pitch;
+  D.k0 = h->k0;
+  D.k1 = h->k1;
+  D.ring = h->ring ? 1u : 0u;
+  D.gpi = h->gpi;
+  D.core = h->core;
+  D.halo = h->halo;
+  D.tau = h->tau;
+  D.n_seg = h->n_seg;
+  D.n_begin = (uint32_t)n_begin;
+  D.n_end = (uint32_t)n_end;
+  D.n_rec = (uint32_t)(rj - ri);
+  D.buf0 = h->buf[h->cur];
+  D.buf1 = h->buf[1 - h->cur];
+  D.rec_sub = h->d_rec_sub ? h->d_rec_sub + ri : nullptr;
+  D.rec_total = h->d_rec_total ? h->d_rec_total + slot : nullptr;
+  D.rec_sample = h->per_sample ? h->d_rec_sample + slot * (size_t)h->S : nullptr;
+  D.done = h->d_done;
+  D.rk = pcpdk::make_round_keys(h->k0, h->k1);
+  D.T = h->T;
 }
 
 // The error word of the engine: 0, or a device-side wait that ran out of its budget.
@@ -719,3 +750,236 @@ extern "C" int pcpd_sweep_noalloc(uint32_t *lat_in, uint32_t *lat_out, uint32_t 
   }
   return PCPD_OK;
 }
+
+// ------------------------------------------------------------------------------------------
+// Batches: many instances (any L, samples, p, d, seed, step count, records) in one persistent
+// launch of the engine over an explicit item list.
+// ------------------------------------------------------------------------------------------
+struct pcpd_batch {
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<pcpd_t *> inst;
+  std::vector<uint64_t> steps;
+  std::vector<std::vector<uint64_t>> rec;
+  unsigned long long *d_items = nullptr;
+  size_t items_cap = 0;
+  uint32_t *d_ctl = nullptr;   // work counter, error word
+  bool ran = false;
+  uint32_t last_threads = 0;
+  size_t last_items = 0;
+};
+
+namespace {
+std::mutex g_batch_mu;   // the constant-memory descriptor table serves one batch launch at a time
+}
+
+extern "C" {
+
+int pcpd_batch_create(void *stream, pcpd_batch_t **out) {
+  if (!out) return fail(PCPD_EINVAL, "NULL argument");
+  *out = nullptr;
+  int rc = device_check();
+  if (rc) return rc;
+  pcpd_batch_t *b = new pcpd_batch();
+  if (stream) {
+    b->stream = (cudaStream_t)stream;
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete b;
+      return fail(PCPD_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+    }
+    b->own_stream = true;
+  }
+  cudaError_t e = cudaMalloc(&b->d_ctl, 2 * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_ctl, 0, 2 * sizeof(uint32_t), b->stream);
+  if (e != cudaSuccess) {
+    pcpd_batch_destroy(b);
+    return fail(PCPD_ENOMEM, "batch control words: %s", cudaGetErrorString(e));
+  }
+  *out = b;
+  return PCPD_OK;
+}
+
+void pcpd_batch_destroy(pcpd_batch_t *b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  for (pcpd_t *h : b->inst) pcpd_destroy(h);
+  cudaFree(b->d_items);
+  cudaFree(b->d_ctl);
+  if (b->own_stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+int pcpd_batch_add(pcpd_batch_t *b, const pcpd_params *prm, uint64_t steps_mcs,
+                   const uint64_t *record_times_mcs, size_t n_times, size_t *index_out) {
+  if (!b || !prm) return fail(PCPD_EINVAL, "NULL argument");
+  if (b->ran) return fail(PCPD_ESTATE, "batch already ran");
+  if (n_times && !record_times_mcs) return fail(PCPD_EINVAL, "record_times_mcs is NULL");
+  for (size_t i = 0; i < n_times; ++i) {
+    if (i && record_times_mcs[i] <= record_times_mcs[i - 1]) return fail(PCPD_EINVAL, "record times must increase");
+    if (record_times_mcs[i] == 0 || record_times_mcs[i] > steps_mcs)
+      return fail(PCPD_EINVAL, "record times must lie in (0, steps_mcs]");
+  }
+  pcpd_params p2 = *prm;
+  p2.stream = b->stream;
+  p2.dev_lattice = nullptr;
+  p2.dev_bytes = 0;
+  pcpd_t *h = nullptr;
+  int rc = pcpd_create_ex(&p2, &h);
+  if (rc) return rc;
+  const uint64_t n_end = steps_mcs ? substep_of_time(h->L, steps_mcs) : 0;
+  if (n_end > 0xFFFFFFFFull) {
+    pcpd_destroy(h);
+    return fail(PCPD_EINVAL, "sub-step count would reach 2^32");
+  }
+  b->inst.push_back(h);
+  b->steps.push_back(steps_mcs);
+  b->rec.emplace_back(record_times_mcs, record_times_mcs + n_times);
+  if (index_out) *index_out = b->inst.size() - 1;
+  return PCPD_OK;
+}
+
+int pcpd_batch_run(pcpd_batch_t *b) {
+  if (!b) return fail(PCPD_EINVAL, "NULL batch");
+  if (b->ran) return fail(PCPD_ESTATE, "batch already ran");
+  int dev = 0, sms = 0, optin = 0;
+  CU(cudaGetDevice(&dev));
+  CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const size_t n = b->inst.size();
+  // per instance: records, flags, epochs
+  std::vector<uint64_t> n_end(n), epochs(n);
+  for (size_t i = 0; i < n; ++i) {
+    pcpd_t *h = b->inst[i];
+    n_end[i] = b->steps[i] ? substep_of_time(h->L, b->steps[i]) : 0;
+    epochs[i] = (n_end[i] + h->tau - 1) / h->tau;
+    if (epochs[i] >= (1u << 24)) return fail(PCPD_EINVAL, "instance %zu needs too many epochs", i);
+    const std::vector<uint64_t> &t = b->rec[i];
+    int rc = ensure_records(h, t.size());
+    if (rc) return rc;
+    if (!t.empty()) {
+      rc = ensure_rec_sub(h, t.size());
+      if (rc) return rc;
+      std::vector<uint32_t> s32;
+      for (uint64_t x : t) s32.push_back((uint32_t)substep_of_time(h->L, x));
+      CU(cudaMemcpyAsync(h->d_rec_sub, s32.data(), s32.size() * 4, cudaMemcpyHostToDevice, b->stream));
+    }
+    CU(cudaMemsetAsync(h->d_done, 0, (h->tiles + 2) * sizeof(uint32_t), b->stream));
+  }
+  // launches of at most kMaxBatchInst instances; in each, whole-ring items first (longest
+  // first), then segmented epochs interleaved across instances, epoch by epoch
+  std::lock_guard<std::mutex> lock(g_batch_mu);
+  for (size_t c0 = 0; c0 < n; c0 += pcpdk::kMaxBatchInst) {
+    const size_t c1 = std::min(n, c0 + (size_t)pcpdk::kMaxBatchInst);
+    std::vector<pcpdk::InstDesc> desc(c1 - c0);
+    size_t tile_words = 0;
+    for (size_t i = c0; i < c1; ++i) {
+      pcpd_t *h = b->inst[i];
+      fill_desc(h, desc[i - c0], 0, n_end[i], 0, b->rec[i].size(), 0);
+      tile_words = std::max(tile_words, h->tile_words);
+    }
+    std::vector<std::pair<double, unsigned long long>> ring_items;
+    std::vector<unsigned long long> items;
+    uint64_t max_ep = 0;
+    for (size_t i = c0; i < c1; ++i) max_ep = std::max(max_ep, b->inst[i]->ring ? 0 : epochs[i]);
+    for (size_t i = c0; i < c1; ++i) {
+      pcpd_t *h = b->inst[i];
+      if (!h->ring) continue;
+      for (uint64_t e = 0; e < epochs[i]; ++e)
+        for (uint32_t t = 0; t < h->tiles; ++t)
+          ring_items.push_back({-(double)h->gpi * h->K * (double)std::min<uint64_t>(h->tau, n_end[i] - e * h->tau) +
+                                    1e-9 * (double)e,
+                                pcpdk::pack_item((uint32_t)(i - c0), (uint32_t)e, t)});
+    }
+    // longest whole-ring work first; a later epoch of the same tile always sorts after its
+    // predecessor because every epoch but the last is full length
+    std::stable_sort(ring_items.begin(), ring_items.end(),
+                     [](const std::pair<double, unsigned long long> &a, const std::pair<double, unsigned long long> &c) {
+                       const uint32_t ea = (uint32_t)((a.second >> 24) & 0xFFFFFFu), ec = (uint32_t)((c.second >> 24) & 0xFFFFFFu);
+                       if (ea != ec) return ea < ec;
+                       return a.first < c.first;
+                     });
+    // Segmented instances are chains of epochs; whole-ring items are independent.  Start every
+    // chain at once and spread the ring items (longest first) between the epochs, so that a
+    // CTA reaching an epoch item finds its predecessors done and the chains do not form the
+    // tail of the launch.
+    const size_t per_round = max_ep ? (ring_items.size() + max_ep - 1) / max_ep : ring_items.size();
+    size_t next_ring = 0;
+    auto add_ring = [&](size_t count) {
+      for (size_t q = 0; q < count && next_ring < ring_items.size(); ++q) items.push_back(ring_items[next_ring++].second);
+    };
+    for (uint64_t e = 0; e < max_ep; ++e) {
+      if (e > 0) add_ring(per_round);
+      for (size_t i = c0; i < c1; ++i) {
+        pcpd_t *h = b->inst[i];
+        if (h->ring || e >= epochs[i]) continue;
+        for (uint32_t t = 0; t < h->tiles; ++t) items.push_back(pcpdk::pack_item((uint32_t)(i - c0), (uint32_t)e, t));
+      }
+    }
+    add_ring(ring_items.size());
+    if (items.empty()) continue;
+    if (items.size() > b->items_cap) {
+      CU(cudaStreamSynchronize(b->stream));
+      cudaFree(b->d_items);
+      b->d_items = nullptr;
+      CU(cudaMalloc(&b->d_items, items.size() * sizeof(unsigned long long)));
+      b->items_cap = items.size();
+    }
+    CU(cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice,
+                       b->stream));
+    CU(cudaMemcpyToSymbolAsync(pcpdk::c_inst, desc.data(), desc.size() * sizeof(pcpdk::InstDesc), 0,
+                               cudaMemcpyHostToDevice, b->stream));
+    CU(cudaMemsetAsync(b->d_ctl, 0, sizeof(uint32_t), b->stream));   // work counter
+    pcpdk::BatchParams B;
+    memset(&B, 0, sizeof B);
+    B.items = b->d_items;
+    B.n_items = (uint32_t)items.size();
+    B.counter = b->d_ctl;
+    B.err = b->d_ctl + 1;
+    B.tile_words = (uint32_t)tile_words;
+    B.spin_limit = kSpinLimit;
+    const uint32_t threads = 1024;
+    const size_t dyn = 4 * (tile_words + pcpdk::sweep_queue_words(32));
+    if (dyn + kStaticSmem > (size_t)optin) return fail(PCPD_EINVAL, "batch tile exceeds shared memory");
+    CU(cudaFuncSetAttribute(pcpdk::k_sweep_persistent<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    int per_sm = 0;
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcpdk::k_sweep_persistent<true>, threads, dyn));
+    if (per_sm < 1) return fail(PCPD_EINVAL, "batch plan does not fit one CTA per SM");
+    const int grid = (int)std::min<uint64_t>((uint64_t)per_sm * sms, items.size());
+    pcpdk::k_sweep_persistent<true><<<grid, threads, dyn, b->stream>>>(B);
+    CU(cudaGetLastError());
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    // the next chunk rewrites the constant table: finish this launch first
+    CU(cudaStreamSynchronize(b->stream));
+    uint32_t err = 0;
+    CU(cudaMemcpy(&err, b->d_ctl + 1, 4, cudaMemcpyDeviceToHost));
+    if (err) return fail(PCPD_ETIMEOUT, "device wait ran out of its budget (code %u)", err);
+    b->last_threads = threads;
+    b->last_items += items.size();
+  }
+  for (size_t i = 0; i < n; ++i) {
+    pcpd_t *h = b->inst[i];
+    if (epochs[i] & 1u) h->cur = 1 - h->cur;
+    h->n_now = n_end[i];
+    h->t_now = b->steps[i];
+    for (uint64_t t : b->rec[i]) h->rec_times.push_back(t);
+  }
+  b->ran = true;
+  return PCPD_OK;
+}
+
+int pcpd_batch_counts(const pcpd_batch_t *b, size_t i, uint64_t *counts_out, size_t n) {
+  if (!b || i >= b->inst.size()) return fail(PCPD_EINVAL, "no instance %zu", i);
+  if (!b->ran) return fail(PCPD_ESTATE, "batch has not run");
+  return pcpd_density(b->inst[i], nullptr, counts_out, n);
+}
+
+int pcpd_batch_lattice(const pcpd_batch_t *b, size_t i, uint32_t *host_out) {
+  if (!b || i >= b->inst.size()) return fail(PCPD_EINVAL, "no instance %zu", i);
+  return pcpd_get_lattice(b->inst[i], host_out);
+}
+
+size_t pcpd_batch_size(const pcpd_batch_t *b) { return b ? b->inst.size() : 0; }
+
+}  // extern "C"

@@ -57,6 +57,13 @@ SIGNATURES = [
     ("pcpd_substep_of_time", C.c_uint64, [C.c_uint32, C.c_uint64]),
     ("pcpd_dev_philox", C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_size_t, C.c_void_p]),
     ("pcpd_dev_rate_masks", C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_void_p, C.c_size_t, C.c_void_p]),
+    ("pcpd_batch_create", C.c_int, [C.c_void_p, C.POINTER(C.c_void_p)]),
+    ("pcpd_batch_add", C.c_int, [C.c_void_p, C.POINTER(Params), C.c_uint64, _u64p, C.c_size_t, C.POINTER(C.c_size_t)]),
+    ("pcpd_batch_run", C.c_int, [C.c_void_p]),
+    ("pcpd_batch_size", C.c_size_t, [C.c_void_p]),
+    ("pcpd_batch_counts", C.c_int, [C.c_void_p, C.c_size_t, _u64p, C.c_size_t]),
+    ("pcpd_batch_lattice", C.c_int, [C.c_void_p, C.c_size_t, _u32p]),
+    ("pcpd_batch_destroy", None, [C.c_void_p]),
     ("pcpd_sweep_noalloc", C.c_int, [C.c_void_p, C.c_void_p, C.c_uint32, C.c_uint32, C.c_double, C.c_double,
                                      C.c_uint64, C.c_uint64, C.c_uint64, C.c_void_p]),
 ]
@@ -200,6 +207,57 @@ class Pcpd:
 
     def sync(self):
         _check(load().pcpd_sync(self._h))
+
+
+class Batch:
+    """Many independent instances run by one persistent launch (pcpd_batch_*)."""
+
+    def __init__(self, stream=None):
+        h = C.c_void_p()
+        s = C.c_void_p(int(getattr(stream, "cuda_stream", stream))) if stream is not None else None
+        _check(load().pcpd_batch_create(s, C.byref(h)))
+        self._h = h
+        self._meta = []
+
+    def add(self, L: int, samples: int, p: float, d: float, seed: int, steps_mcs: int,
+            record_times=(), init: int = INIT_FULL, plan_threads: int = 0, plan_seg_sites: int = 0,
+            plan_tau: int = 0) -> int:
+        prm = Params()
+        prm.L, prm.samples, prm.p, prm.d, prm.seed, prm.init = L, samples, p, d, seed, init
+        prm.plan_threads, prm.plan_seg_sites, prm.plan_tau = plan_threads, plan_seg_sites, plan_tau
+        t = np.ascontiguousarray(record_times, dtype=np.uint64)
+        idx = C.c_size_t()
+        _check(load().pcpd_batch_add(self._h, C.byref(prm), steps_mcs, _ptr(t, C.c_uint64) if t.size else None,
+                                     t.size, C.byref(idx)))
+        self._meta.append((L, samples, len(t)))
+        return int(idx.value)
+
+    def run(self):
+        _check(load().pcpd_batch_run(self._h))
+
+    def counts(self, i: int) -> np.ndarray:
+        n = self._meta[i][2]
+        c = np.zeros(n, dtype=np.uint64)
+        if n:
+            _check(load().pcpd_batch_counts(self._h, i, _ptr(c, C.c_uint64), n))
+        return c
+
+    def lattice(self, i: int) -> np.ndarray:
+        L, S, _ = self._meta[i]
+        out = np.zeros((S // 32, L), dtype=np.uint32)
+        _check(load().pcpd_batch_lattice(self._h, i, _ptr(out, C.c_uint32)))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().pcpd_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def dev_philox(ctr_dev, seed: int, out_dev, n: int, stream=None):
