@@ -184,6 +184,60 @@ int pcpd_batch_lattice(const pcpd_batch_t *b, size_t i, uint32_t *host_out);
 /* Release the batch and all its instances.  NULL-safe. */
 void pcpd_batch_destroy(pcpd_batch_t *b);
 
+/* ---- serving: continuous batching of simulation requests ----
+ * A host thread of the library owns the GPU work.  Requests wait in FIFO order until a slot
+ * (at most max_active on the GPU) and the device-memory budget allow their admission; each
+ * round then advances every active request by at most chunk_attempts attempted updates in
+ * one engine launch, so the requests' work overlaps on the device, while each request's
+ * lattice and clock (its random-number counter) stay on the device between rounds.  A
+ * finished request frees its slot and memory for the queue.  Results are bit-identical to
+ * the same request run alone. */
+typedef struct pcpd_server pcpd_server_t;
+
+typedef struct pcpd_server_config {
+    size_t hbm_budget_bytes;   /* device memory for admitted requests (lattices, records) */
+    uint32_t max_active;       /* requests on the GPU at once, 1..128 */
+    uint64_t chunk_attempts;   /* attempted updates per request per round (> 0) */
+    void *stream;              /* cudaStream_t for the server's work; NULL = its own */
+} pcpd_server_config;
+
+typedef struct pcpd_server_stats {
+    uint64_t submitted, completed, failed;
+    uint64_t rounds;           /* engine rounds run */
+    double busy_seconds;       /* wall time inside rounds */
+    unsigned long long attempts;  /* attempted site updates done */
+    uint64_t active, queued;   /* now */
+    size_t mem_used_bytes;     /* now */
+} pcpd_server_stats;
+
+/* Start a server (its thread begins waiting for requests). */
+int pcpd_server_start(const pcpd_server_config *cfg, pcpd_server_t **out);
+
+/* Queue a request (pcpd_params as for pcpd_create_ex; stream/dev_lattice ignored) for
+ * steps_mcs MCS with records at record_times_mcs[0..n_times) (strictly increasing, in
+ * (0, steps_mcs]; copied).  keep_lattice != 0 keeps the final lattice for pcpd_server_result.
+ * Thread-safe.  *id_out receives the request id. */
+int pcpd_server_submit(pcpd_server_t *sv, const pcpd_params *prm, uint64_t steps_mcs,
+                       const uint64_t *record_times_mcs, size_t n_times, int keep_lattice,
+                       uint64_t *id_out);
+
+/* State of a request: 0 queued, 1 on the GPU, 2 done, 3 failed. */
+int pcpd_server_poll(pcpd_server_t *sv, uint64_t id, int *state_out);
+
+/* Wait for request id and copy its first n record counts (nullable), its final lattice
+ * (canonical layout, nullable; needs keep_lattice), its latency from submission to result
+ * (nullable) and the part of it spent queued before admission (nullable). */
+int pcpd_server_result(pcpd_server_t *sv, uint64_t id, uint64_t *counts_out, size_t n,
+                       uint32_t *lattice_out, double *latency_s, double *queue_s);
+
+/* Wait until every submitted request has finished or failed. */
+int pcpd_server_wait_idle(pcpd_server_t *sv);
+
+int pcpd_server_get_stats(pcpd_server_t *sv, pcpd_server_stats *out);
+
+/* Stop the thread; requests not finished fail with "server stopped".  NULL-safe. */
+void pcpd_server_stop(pcpd_server_t *sv);
+
 /* ---- allocation-free sweep ----
  * Advance a caller-owned lattice by n_substeps sub-steps without allocating any memory.
  * The paper has no counterpart: this is an entry point for callers that cannot let a

@@ -8,7 +8,13 @@
 #include <cstdio>
 #include <algorithm>
 #include <cstring>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <memory>
 #include <mutex>
+#include <thread>
+#include <unordered_map>
 #include <string>
 #include <vector>
 
@@ -765,13 +771,136 @@ struct pcpd_batch {
   size_t items_cap = 0;
   uint32_t *d_ctl = nullptr;   // work counter, error word
   bool ran = false;
-  uint32_t last_threads = 0;
-  size_t last_items = 0;
 };
 
 namespace {
 std::mutex g_batch_mu;   // the constant-memory descriptor table serves one batch launch at a time
+
+// One instance's share of a multi-instance launch: advance h from h->n_now to n_end; its
+// record sub-steps are rec_sub (all of them, increasing, already on the device in
+// h->d_rec_sub); records rec_first.. that fall in (n_now, n_end] go to slots slot0.. .
+struct MultiTarget {
+  pcpd_t *h = nullptr;
+  uint64_t n_end = 0;
+  std::vector<uint64_t> rec_sub;
+  size_t rec_first = 0;
+  size_t slot0 = 0;
+  size_t rec_taken = 0;   // out: records that fell in this launch
+};
+
+// Advance every target in engine launches of at most kMaxBatchInst instances each; the item
+// list starts every segmented chain at once and spreads the whole-ring items (longest first)
+// between its epochs.  Waits for completion; updates each handle's buffer and clock.
+int run_multi(cudaStream_t stream, uint32_t *d_ctl, unsigned long long **d_items, size_t *items_cap,
+              std::vector<MultiTarget> &tg) {
+  int dev = 0, sms = 0, optin = 0;
+  CU(cudaGetDevice(&dev));
+  CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const size_t n = tg.size();
+  std::vector<uint64_t> epochs(n);
+  for (size_t i = 0; i < n; ++i) {
+    pcpd_t *h = tg[i].h;
+    if (tg[i].n_end < h->n_now) return fail(PCPD_EINVAL, "target sub-step behind the clock");
+    if (tg[i].n_end > 0xFFFFFFFFull) return fail(PCPD_EINVAL, "sub-step count would reach 2^32");
+    epochs[i] = (tg[i].n_end - h->n_now + h->tau - 1) / h->tau;
+    if (epochs[i] >= (1u << 24)) return fail(PCPD_EINVAL, "instance %zu needs too many epochs", i);
+    CU(cudaMemsetAsync(h->d_done, 0, (h->tiles + 2) * sizeof(uint32_t), stream));
+    size_t rj = tg[i].rec_first;
+    while (rj < tg[i].rec_sub.size() && tg[i].rec_sub[rj] <= tg[i].n_end) ++rj;
+    tg[i].rec_taken = rj - tg[i].rec_first;
+  }
+  std::lock_guard<std::mutex> lock(g_batch_mu);
+  for (size_t c0 = 0; c0 < n; c0 += pcpdk::kMaxBatchInst) {
+    const size_t c1 = std::min(n, c0 + (size_t)pcpdk::kMaxBatchInst);
+    std::vector<pcpdk::InstDesc> desc(c1 - c0);
+    size_t tile_words = 0;
+    for (size_t i = c0; i < c1; ++i) {
+      pcpd_t *h = tg[i].h;
+      fill_desc(h, desc[i - c0], h->n_now, tg[i].n_end, tg[i].rec_first, tg[i].rec_first + tg[i].rec_taken,
+                tg[i].slot0);
+      tile_words = std::max(tile_words, h->tile_words);
+    }
+    std::vector<std::pair<double, unsigned long long>> ring_items;
+    std::vector<unsigned long long> items;
+    uint64_t max_ep = 0;
+    for (size_t i = c0; i < c1; ++i) max_ep = std::max(max_ep, tg[i].h->ring ? 0 : epochs[i]);
+    for (size_t i = c0; i < c1; ++i) {
+      pcpd_t *h = tg[i].h;
+      if (!h->ring) continue;
+      for (uint64_t e = 0; e < epochs[i]; ++e) {
+        const uint64_t len = std::min<uint64_t>(h->tau, tg[i].n_end - h->n_now - e * h->tau);
+        for (uint32_t t = 0; t < h->tiles; ++t)
+          ring_items.push_back({-(double)h->gpi * h->K * (double)len, pcpdk::pack_item((uint32_t)(i - c0), (uint32_t)e, t)});
+      }
+    }
+    // longest first; a later epoch of a tile sorts after all earlier epochs
+    std::stable_sort(ring_items.begin(), ring_items.end(),
+                     [](const std::pair<double, unsigned long long> &a, const std::pair<double, unsigned long long> &c) {
+                       const uint32_t ea = (uint32_t)((a.second >> 24) & 0xFFFFFFu), ec = (uint32_t)((c.second >> 24) & 0xFFFFFFu);
+                       if (ea != ec) return ea < ec;
+                       return a.first < c.first;
+                     });
+    const size_t per_round = max_ep ? (ring_items.size() + max_ep - 1) / max_ep : ring_items.size();
+    size_t next_ring = 0;
+    auto add_ring = [&](size_t count) {
+      for (size_t q = 0; q < count && next_ring < ring_items.size(); ++q) items.push_back(ring_items[next_ring++].second);
+    };
+    for (uint64_t e = 0; e < max_ep; ++e) {
+      if (e > 0) add_ring(per_round);
+      for (size_t i = c0; i < c1; ++i) {
+        pcpd_t *h = tg[i].h;
+        if (h->ring || e >= epochs[i]) continue;
+        for (uint32_t t = 0; t < h->tiles; ++t) items.push_back(pcpdk::pack_item((uint32_t)(i - c0), (uint32_t)e, t));
+      }
+    }
+    add_ring(ring_items.size());
+    if (items.empty()) continue;
+    if (items.size() > *items_cap) {
+      CU(cudaStreamSynchronize(stream));
+      cudaFree(*d_items);
+      *d_items = nullptr;
+      CU(cudaMalloc(d_items, items.size() * sizeof(unsigned long long)));
+      *items_cap = items.size();
+    }
+    CU(cudaMemcpyAsync(*d_items, items.data(), items.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice,
+                       stream));
+    CU(cudaMemcpyToSymbolAsync(pcpdk::c_inst, desc.data(), desc.size() * sizeof(pcpdk::InstDesc), 0,
+                               cudaMemcpyHostToDevice, stream));
+    CU(cudaMemsetAsync(d_ctl, 0, sizeof(uint32_t), stream));   // work counter
+    pcpdk::BatchParams B;
+    memset(&B, 0, sizeof B);
+    B.items = *d_items;
+    B.n_items = (uint32_t)items.size();
+    B.counter = d_ctl;
+    B.err = d_ctl + 1;
+    B.tile_words = (uint32_t)tile_words;
+    B.spin_limit = kSpinLimit;
+    const uint32_t threads = 1024;
+    const size_t dyn = 4 * (tile_words + pcpdk::sweep_queue_words(32));
+    if (dyn + kStaticSmem > (size_t)optin) return fail(PCPD_EINVAL, "batch tile exceeds shared memory");
+    CU(cudaFuncSetAttribute(pcpdk::k_sweep_persistent<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    int per_sm = 0;
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcpdk::k_sweep_persistent<true>, threads, dyn));
+    if (per_sm < 1) return fail(PCPD_EINVAL, "batch plan does not fit one CTA per SM");
+    const int grid = (int)std::min<uint64_t>((uint64_t)per_sm * sms, items.size());
+    pcpdk::k_sweep_persistent<true><<<grid, threads, dyn, stream>>>(B);
+    CU(cudaGetLastError());
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    // the next launch rewrites the constant table and the host vectors go out of scope
+    CU(cudaStreamSynchronize(stream));
+    uint32_t err = 0;
+    CU(cudaMemcpy(&err, d_ctl + 1, 4, cudaMemcpyDeviceToHost));
+    if (err) return fail(PCPD_ETIMEOUT, "device wait ran out of its budget (code %u)", err);
+  }
+  for (size_t i = 0; i < n; ++i) {
+    pcpd_t *h = tg[i].h;
+    if (epochs[i] & 1u) h->cur = 1 - h->cur;
+    h->n_now = tg[i].n_end;
+  }
+  return PCPD_OK;
 }
+}  // namespace
 
 extern "C" {
 
@@ -843,125 +972,29 @@ int pcpd_batch_add(pcpd_batch_t *b, const pcpd_params *prm, uint64_t steps_mcs,
 int pcpd_batch_run(pcpd_batch_t *b) {
   if (!b) return fail(PCPD_EINVAL, "NULL batch");
   if (b->ran) return fail(PCPD_ESTATE, "batch already ran");
-  int dev = 0, sms = 0, optin = 0;
-  CU(cudaGetDevice(&dev));
-  CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   const size_t n = b->inst.size();
-  // per instance: records, flags, epochs
-  std::vector<uint64_t> n_end(n), epochs(n);
+  std::vector<MultiTarget> tg(n);
   for (size_t i = 0; i < n; ++i) {
     pcpd_t *h = b->inst[i];
-    n_end[i] = b->steps[i] ? substep_of_time(h->L, b->steps[i]) : 0;
-    epochs[i] = (n_end[i] + h->tau - 1) / h->tau;
-    if (epochs[i] >= (1u << 24)) return fail(PCPD_EINVAL, "instance %zu needs too many epochs", i);
-    const std::vector<uint64_t> &t = b->rec[i];
-    int rc = ensure_records(h, t.size());
+    tg[i].h = h;
+    tg[i].n_end = b->steps[i] ? substep_of_time(h->L, b->steps[i]) : 0;
+    int rc = ensure_records(h, b->rec[i].size());
     if (rc) return rc;
-    if (!t.empty()) {
-      rc = ensure_rec_sub(h, t.size());
+    if (!b->rec[i].empty()) {
+      rc = ensure_rec_sub(h, b->rec[i].size());
       if (rc) return rc;
       std::vector<uint32_t> s32;
-      for (uint64_t x : t) s32.push_back((uint32_t)substep_of_time(h->L, x));
+      for (uint64_t x : b->rec[i]) s32.push_back((uint32_t)substep_of_time(h->L, x));
       CU(cudaMemcpyAsync(h->d_rec_sub, s32.data(), s32.size() * 4, cudaMemcpyHostToDevice, b->stream));
+      tg[i].rec_sub.assign(s32.begin(), s32.end());
     }
-    CU(cudaMemsetAsync(h->d_done, 0, (h->tiles + 2) * sizeof(uint32_t), b->stream));
+    tg[i].rec_first = 0;
+    tg[i].slot0 = 0;
   }
-  // launches of at most kMaxBatchInst instances; in each, whole-ring items first (longest
-  // first), then segmented epochs interleaved across instances, epoch by epoch
-  std::lock_guard<std::mutex> lock(g_batch_mu);
-  for (size_t c0 = 0; c0 < n; c0 += pcpdk::kMaxBatchInst) {
-    const size_t c1 = std::min(n, c0 + (size_t)pcpdk::kMaxBatchInst);
-    std::vector<pcpdk::InstDesc> desc(c1 - c0);
-    size_t tile_words = 0;
-    for (size_t i = c0; i < c1; ++i) {
-      pcpd_t *h = b->inst[i];
-      fill_desc(h, desc[i - c0], 0, n_end[i], 0, b->rec[i].size(), 0);
-      tile_words = std::max(tile_words, h->tile_words);
-    }
-    std::vector<std::pair<double, unsigned long long>> ring_items;
-    std::vector<unsigned long long> items;
-    uint64_t max_ep = 0;
-    for (size_t i = c0; i < c1; ++i) max_ep = std::max(max_ep, b->inst[i]->ring ? 0 : epochs[i]);
-    for (size_t i = c0; i < c1; ++i) {
-      pcpd_t *h = b->inst[i];
-      if (!h->ring) continue;
-      for (uint64_t e = 0; e < epochs[i]; ++e)
-        for (uint32_t t = 0; t < h->tiles; ++t)
-          ring_items.push_back({-(double)h->gpi * h->K * (double)std::min<uint64_t>(h->tau, n_end[i] - e * h->tau) +
-                                    1e-9 * (double)e,
-                                pcpdk::pack_item((uint32_t)(i - c0), (uint32_t)e, t)});
-    }
-    // longest whole-ring work first; a later epoch of the same tile always sorts after its
-    // predecessor because every epoch but the last is full length
-    std::stable_sort(ring_items.begin(), ring_items.end(),
-                     [](const std::pair<double, unsigned long long> &a, const std::pair<double, unsigned long long> &c) {
-                       const uint32_t ea = (uint32_t)((a.second >> 24) & 0xFFFFFFu), ec = (uint32_t)((c.second >> 24) & 0xFFFFFFu);
-                       if (ea != ec) return ea < ec;
-                       return a.first < c.first;
-                     });
-    // Segmented instances are chains of epochs; whole-ring items are independent.  Start every
-    // chain at once and spread the ring items (longest first) between the epochs, so that a
-    // CTA reaching an epoch item finds its predecessors done and the chains do not form the
-    // tail of the launch.
-    const size_t per_round = max_ep ? (ring_items.size() + max_ep - 1) / max_ep : ring_items.size();
-    size_t next_ring = 0;
-    auto add_ring = [&](size_t count) {
-      for (size_t q = 0; q < count && next_ring < ring_items.size(); ++q) items.push_back(ring_items[next_ring++].second);
-    };
-    for (uint64_t e = 0; e < max_ep; ++e) {
-      if (e > 0) add_ring(per_round);
-      for (size_t i = c0; i < c1; ++i) {
-        pcpd_t *h = b->inst[i];
-        if (h->ring || e >= epochs[i]) continue;
-        for (uint32_t t = 0; t < h->tiles; ++t) items.push_back(pcpdk::pack_item((uint32_t)(i - c0), (uint32_t)e, t));
-      }
-    }
-    add_ring(ring_items.size());
-    if (items.empty()) continue;
-    if (items.size() > b->items_cap) {
-      CU(cudaStreamSynchronize(b->stream));
-      cudaFree(b->d_items);
-      b->d_items = nullptr;
-      CU(cudaMalloc(&b->d_items, items.size() * sizeof(unsigned long long)));
-      b->items_cap = items.size();
-    }
-    CU(cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice,
-                       b->stream));
-    CU(cudaMemcpyToSymbolAsync(pcpdk::c_inst, desc.data(), desc.size() * sizeof(pcpdk::InstDesc), 0,
-                               cudaMemcpyHostToDevice, b->stream));
-    CU(cudaMemsetAsync(b->d_ctl, 0, sizeof(uint32_t), b->stream));   // work counter
-    pcpdk::BatchParams B;
-    memset(&B, 0, sizeof B);
-    B.items = b->d_items;
-    B.n_items = (uint32_t)items.size();
-    B.counter = b->d_ctl;
-    B.err = b->d_ctl + 1;
-    B.tile_words = (uint32_t)tile_words;
-    B.spin_limit = kSpinLimit;
-    const uint32_t threads = 1024;
-    const size_t dyn = 4 * (tile_words + pcpdk::sweep_queue_words(32));
-    if (dyn + kStaticSmem > (size_t)optin) return fail(PCPD_EINVAL, "batch tile exceeds shared memory");
-    CU(cudaFuncSetAttribute(pcpdk::k_sweep_persistent<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
-    int per_sm = 0;
-    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcpdk::k_sweep_persistent<true>, threads, dyn));
-    if (per_sm < 1) return fail(PCPD_EINVAL, "batch plan does not fit one CTA per SM");
-    const int grid = (int)std::min<uint64_t>((uint64_t)per_sm * sms, items.size());
-    pcpdk::k_sweep_persistent<true><<<grid, threads, dyn, b->stream>>>(B);
-    CU(cudaGetLastError());
-    g_launches.fetch_add(1, std::memory_order_relaxed);
-    // the next chunk rewrites the constant table: finish this launch first
-    CU(cudaStreamSynchronize(b->stream));
-    uint32_t err = 0;
-    CU(cudaMemcpy(&err, b->d_ctl + 1, 4, cudaMemcpyDeviceToHost));
-    if (err) return fail(PCPD_ETIMEOUT, "device wait ran out of its budget (code %u)", err);
-    b->last_threads = threads;
-    b->last_items += items.size();
-  }
+  int rc = run_multi(b->stream, b->d_ctl, &b->d_items, &b->items_cap, tg);
+  if (rc) return rc;
   for (size_t i = 0; i < n; ++i) {
     pcpd_t *h = b->inst[i];
-    if (epochs[i] & 1u) h->cur = 1 - h->cur;
-    h->n_now = n_end[i];
     h->t_now = b->steps[i];
     for (uint64_t t : b->rec[i]) h->rec_times.push_back(t);
   }
@@ -981,5 +1014,335 @@ int pcpd_batch_lattice(const pcpd_batch_t *b, size_t i, uint32_t *host_out) {
 }
 
 size_t pcpd_batch_size(const pcpd_batch_t *b) { return b ? b->inst.size() : 0; }
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------------
+// Serving: continuous batching of simulation requests.  A host thread owns the GPU work: it
+// admits queued requests while active slots and the device-memory budget allow, advances
+// every active request by a bounded chunk per round in one engine launch (their work
+// overlaps on the device), keeps each request's lattice and clock on the device between
+// rounds, and retires finished requests, freeing their slot and memory for the queue.
+// ------------------------------------------------------------------------------------------
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+  uint64_t id = 0;
+  pcpd_params prm{};
+  uint64_t steps = 0;
+  std::vector<uint64_t> rec_times;
+  bool keep_lattice = false;
+  Clock::time_point t_submit, t_admit, t_done;
+  int state = 0;  // 0 queued, 1 active, 2 done, 3 failed
+  std::string err;
+  pcpd_t *h = nullptr;
+  uint64_t n_end = 0;
+  std::vector<uint64_t> rec_sub;
+  size_t rec_first = 0;
+  size_t bytes = 0;
+  std::vector<uint64_t> counts;
+  std::vector<uint32_t> lattice;
+};
+
+size_t request_bytes(const pcpd_params &p, size_t n_rec) {
+  const size_t G = p.samples / 32u, pitch = (p.L + 3u) & ~3u;
+  return 2 * G * pitch * 4 + n_rec * 8 + (p.per_sample ? n_rec * (size_t)p.samples * 4 : 0) + 4096;
+}
+
+}  // namespace
+
+struct pcpd_server {
+  pcpd_server_config cfg{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  uint32_t *d_ctl = nullptr;
+  unsigned long long *d_items = nullptr;
+  size_t items_cap = 0;
+  std::thread th;
+  std::mutex mu;
+  std::condition_variable cv, cv_done;
+  bool stop = false;
+  std::deque<Request *> pending;
+  std::vector<Request *> active;
+  std::unordered_map<uint64_t, std::unique_ptr<Request>> all;
+  uint64_t next_id = 1;
+  size_t mem_used = 0;
+  int device = 0;
+  pcpd_server_stats st{};
+  std::string fatal;
+};
+
+namespace {
+
+void server_retire(pcpd_server_t *sv, Request *r, int ok, const std::string &msg) {
+  if (ok) {
+    r->counts.resize(r->rec_times.size());
+    if (!r->counts.empty() && pcpd_density(r->h, nullptr, r->counts.data(), r->counts.size()) != PCPD_OK) {
+      ok = 0;
+      r->err = g_err;
+    }
+    if (ok && r->keep_lattice) {
+      r->lattice.resize((size_t)(r->prm.samples / 32u) * r->prm.L);
+      if (pcpd_get_lattice(r->h, r->lattice.data()) != PCPD_OK) {
+        ok = 0;
+        r->err = g_err;
+      }
+    }
+  } else {
+    r->err = msg;
+  }
+  pcpd_destroy(r->h);
+  r->h = nullptr;
+  std::lock_guard<std::mutex> lock(sv->mu);
+  sv->mem_used -= r->bytes;
+  r->t_done = Clock::now();
+  r->state = ok ? 2 : 3;
+  if (ok) sv->st.completed++;
+  else sv->st.failed++;
+  sv->cv_done.notify_all();
+}
+
+void server_loop(pcpd_server_t *sv) {
+  cudaSetDevice(sv->device);
+  for (;;) {
+    std::vector<Request *> admit;
+    {
+      std::unique_lock<std::mutex> lock(sv->mu);
+      sv->cv.wait(lock, [&] { return sv->stop || !sv->pending.empty() || !sv->active.empty(); });
+      if (sv->stop) break;
+      // admission: FIFO while a slot and the memory budget are free (an oversized request is
+      // admitted alone so that it cannot block the queue forever)
+      while (!sv->pending.empty() && sv->active.size() + admit.size() < sv->cfg.max_active) {
+        Request *r = sv->pending.front();
+        if (sv->mem_used + r->bytes > sv->cfg.hbm_budget_bytes && !(sv->active.empty() && admit.empty())) break;
+        sv->pending.pop_front();
+        sv->mem_used += r->bytes;
+        admit.push_back(r);
+      }
+    }
+    for (Request *r : admit) {
+      pcpd_params p2 = r->prm;
+      p2.stream = sv->stream;
+      p2.dev_lattice = nullptr;
+      int rc = pcpd_create_ex(&p2, &r->h);
+      if (rc == PCPD_OK) rc = ensure_records(r->h, r->rec_times.size());
+      if (rc == PCPD_OK && !r->rec_times.empty()) {
+        rc = ensure_rec_sub(r->h, r->rec_times.size());
+        std::vector<uint32_t> s32;
+        for (uint64_t t : r->rec_times) {
+          r->rec_sub.push_back(substep_of_time(r->h->L, t));
+          s32.push_back((uint32_t)r->rec_sub.back());
+        }
+        if (rc == PCPD_OK &&
+            cudaMemcpyAsync(r->h->d_rec_sub, s32.data(), s32.size() * 4, cudaMemcpyHostToDevice, sv->stream) != cudaSuccess)
+          rc = PCPD_ECUDA;
+        if (rc == PCPD_OK && cudaStreamSynchronize(sv->stream) != cudaSuccess) rc = PCPD_ECUDA;
+      }
+      r->t_admit = Clock::now();
+      if (rc != PCPD_OK) {
+        server_retire(sv, r, 0, g_err);
+        continue;
+      }
+      r->n_end = r->steps ? substep_of_time(r->h->L, r->steps) : 0;
+      std::lock_guard<std::mutex> lock(sv->mu);
+      r->state = 1;
+      sv->active.push_back(r);
+    }
+    std::vector<Request *> act;
+    {
+      std::lock_guard<std::mutex> lock(sv->mu);
+      act = sv->active;
+    }
+    if (act.empty()) continue;
+    // one round: every active request advances by at most chunk_attempts attempts
+    std::vector<MultiTarget> tg(act.size());
+    unsigned long long round_attempts = 0;
+    for (size_t i = 0; i < act.size(); ++i) {
+      Request *r = act[i];
+      pcpd_t *h = r->h;
+      const unsigned long long per_sub = (unsigned long long)h->S * h->K;
+      uint64_t chunk = sv->cfg.chunk_attempts / (per_sub ? per_sub : 1);
+      if (chunk < 1) chunk = 1;
+      tg[i].h = h;
+      tg[i].n_end = std::min<uint64_t>(r->n_end, h->n_now + chunk);
+      tg[i].rec_sub = r->rec_sub;
+      tg[i].rec_first = r->rec_first;
+      tg[i].slot0 = r->rec_first;
+      round_attempts += per_sub * (tg[i].n_end - h->n_now);
+    }
+    const Clock::time_point t0 = Clock::now();
+    const int rc = run_multi(sv->stream, sv->d_ctl, &sv->d_items, &sv->items_cap, tg);
+    const double dt = std::chrono::duration<double>(Clock::now() - t0).count();
+    {
+      std::lock_guard<std::mutex> lock(sv->mu);
+      sv->st.rounds++;
+      sv->st.busy_seconds += dt;
+      if (rc == PCPD_OK) sv->st.attempts += round_attempts;
+    }
+    for (size_t i = 0; i < act.size(); ++i) {
+      Request *r = act[i];
+      if (rc != PCPD_OK) {
+        {
+          std::lock_guard<std::mutex> lock(sv->mu);
+          sv->active.erase(std::find(sv->active.begin(), sv->active.end(), r));
+        }
+        server_retire(sv, r, 0, g_err);
+        continue;
+      }
+      r->rec_first += tg[i].rec_taken;
+      if (r->h->n_now >= r->n_end) {
+        r->h->t_now = r->steps;
+        r->h->rec_times = r->rec_times;
+        {
+          std::lock_guard<std::mutex> lock(sv->mu);
+          sv->active.erase(std::find(sv->active.begin(), sv->active.end(), r));
+        }
+        server_retire(sv, r, 1, "");
+      }
+    }
+  }
+  // stopped: abandon what is left
+  std::vector<Request *> left;
+  {
+    std::lock_guard<std::mutex> lock(sv->mu);
+    left = sv->active;
+    sv->active.clear();
+    for (Request *r : sv->pending) left.push_back(r);
+    sv->pending.clear();
+  }
+  for (Request *r : left) server_retire(sv, r, 0, "server stopped");
+}
+
+}  // namespace
+
+extern "C" {
+
+int pcpd_server_start(const pcpd_server_config *cfg, pcpd_server_t **out) {
+  if (!cfg || !out) return fail(PCPD_EINVAL, "NULL argument");
+  *out = nullptr;
+  if (cfg->max_active == 0 || cfg->max_active > (uint32_t)pcpdk::kMaxBatchInst)
+    return fail(PCPD_EINVAL, "max_active must be in [1, %d]", pcpdk::kMaxBatchInst);
+  if (cfg->hbm_budget_bytes == 0 || cfg->chunk_attempts == 0) return fail(PCPD_EINVAL, "budget and chunk must be positive");
+  int rc = device_check();
+  if (rc) return rc;
+  pcpd_server_t *sv = new pcpd_server();
+  sv->cfg = *cfg;
+  CU(cudaGetDevice(&sv->device));
+  cudaError_t e = cudaSuccess;
+  if (cfg->stream) {
+    sv->stream = (cudaStream_t)cfg->stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking);
+    sv->own_stream = e == cudaSuccess;
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&sv->d_ctl, 2 * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemsetAsync(sv->d_ctl, 0, 2 * sizeof(uint32_t), sv->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(sv->stream);
+  if (e != cudaSuccess) {
+    if (sv->own_stream) cudaStreamDestroy(sv->stream);
+    cudaFree(sv->d_ctl);
+    delete sv;
+    return fail(PCPD_ECUDA, "server start: %s", cudaGetErrorString(e));
+  }
+  sv->th = std::thread(server_loop, sv);
+  *out = sv;
+  return PCPD_OK;
+}
+
+int pcpd_server_submit(pcpd_server_t *sv, const pcpd_params *prm, uint64_t steps_mcs,
+                       const uint64_t *record_times_mcs, size_t n_times, int keep_lattice, uint64_t *id_out) {
+  if (!sv || !prm || !id_out) return fail(PCPD_EINVAL, "NULL argument");
+  if (n_times && !record_times_mcs) return fail(PCPD_EINVAL, "record_times_mcs is NULL");
+  if (prm->L < 3 || prm->L >= (1u << 30) || prm->samples == 0 || prm->samples % 32 || prm->samples > (1u << 22))
+    return fail(PCPD_EINVAL, "bad L or samples");
+  uint64_t td, tda;
+  int rc = thresholds(prm->p, prm->d, &td, &tda);
+  if (rc) return rc;
+  for (size_t i = 0; i < n_times; ++i) {
+    if (i && record_times_mcs[i] <= record_times_mcs[i - 1]) return fail(PCPD_EINVAL, "record times must increase");
+    if (record_times_mcs[i] == 0 || record_times_mcs[i] > steps_mcs)
+      return fail(PCPD_EINVAL, "record times must lie in (0, steps_mcs]");
+  }
+  if (steps_mcs && substep_of_time(prm->L, steps_mcs) > 0xFFFFFFFFull) return fail(PCPD_EINVAL, "too many sub-steps");
+  std::unique_ptr<Request> r(new Request());
+  r->prm = *prm;
+  r->steps = steps_mcs;
+  r->rec_times.assign(record_times_mcs, record_times_mcs + n_times);
+  r->keep_lattice = keep_lattice != 0;
+  r->bytes = request_bytes(*prm, n_times);
+  r->t_submit = Clock::now();
+  std::lock_guard<std::mutex> lock(sv->mu);
+  if (sv->stop) return fail(PCPD_ESTATE, "server stopped");
+  r->id = sv->next_id++;
+  *id_out = r->id;
+  sv->pending.push_back(r.get());
+  sv->all[r->id] = std::move(r);
+  sv->st.submitted++;
+  sv->cv.notify_all();
+  return PCPD_OK;
+}
+
+int pcpd_server_poll(pcpd_server_t *sv, uint64_t id, int *state_out) {
+  if (!sv || !state_out) return fail(PCPD_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lock(sv->mu);
+  auto it = sv->all.find(id);
+  if (it == sv->all.end()) return fail(PCPD_EINVAL, "unknown request %llu", (unsigned long long)id);
+  *state_out = it->second->state;
+  return PCPD_OK;
+}
+
+int pcpd_server_result(pcpd_server_t *sv, uint64_t id, uint64_t *counts_out, size_t n, uint32_t *lattice_out,
+                       double *latency_s, double *queue_s) {
+  if (!sv) return fail(PCPD_EINVAL, "NULL server");
+  std::unique_lock<std::mutex> lock(sv->mu);
+  auto it = sv->all.find(id);
+  if (it == sv->all.end()) return fail(PCPD_EINVAL, "unknown request %llu", (unsigned long long)id);
+  Request *r = it->second.get();
+  sv->cv_done.wait(lock, [&] { return r->state >= 2; });
+  if (r->state == 3) return fail(PCPD_ESTATE, "request %llu failed: %s", (unsigned long long)id, r->err.c_str());
+  if (n > r->counts.size()) return fail(PCPD_EINVAL, "request has %zu records", r->counts.size());
+  if (counts_out) std::copy(r->counts.begin(), r->counts.begin() + n, counts_out);
+  if (lattice_out) {
+    if (!r->keep_lattice) return fail(PCPD_ESTATE, "lattice was not kept (keep_lattice = 0)");
+    std::copy(r->lattice.begin(), r->lattice.end(), lattice_out);
+  }
+  if (latency_s) *latency_s = std::chrono::duration<double>(r->t_done - r->t_submit).count();
+  if (queue_s) *queue_s = std::chrono::duration<double>(r->t_admit - r->t_submit).count();
+  return PCPD_OK;
+}
+
+int pcpd_server_wait_idle(pcpd_server_t *sv) {
+  if (!sv) return fail(PCPD_EINVAL, "NULL server");
+  std::unique_lock<std::mutex> lock(sv->mu);
+  sv->cv_done.wait(lock, [&] { return sv->st.completed + sv->st.failed == sv->st.submitted; });
+  return PCPD_OK;
+}
+
+int pcpd_server_get_stats(pcpd_server_t *sv, pcpd_server_stats *out) {
+  if (!sv || !out) return fail(PCPD_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lock(sv->mu);
+  *out = sv->st;
+  out->active = sv->active.size();
+  out->queued = sv->pending.size();
+  out->mem_used_bytes = sv->mem_used;
+  return PCPD_OK;
+}
+
+void pcpd_server_stop(pcpd_server_t *sv) {
+  if (!sv) return;
+  {
+    std::lock_guard<std::mutex> lock(sv->mu);
+    sv->stop = true;
+    sv->cv.notify_all();
+  }
+  if (sv->th.joinable()) sv->th.join();
+  cudaStreamSynchronize(sv->stream);
+  cudaFree(sv->d_items);
+  cudaFree(sv->d_ctl);
+  if (sv->own_stream) cudaStreamDestroy(sv->stream);
+  delete sv;
+}
 
 }  // extern "C"

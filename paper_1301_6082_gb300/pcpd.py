@@ -35,6 +35,17 @@ class Params(C.Structure):
                 ("plan_threads", C.c_uint32), ("plan_seg_sites", C.c_uint32), ("plan_tau", C.c_uint32)]
 
 
+class ServerConfig(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_active", C.c_uint32), ("chunk_attempts", C.c_uint64),
+                ("stream", C.c_void_p)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("failed", C.c_uint64),
+                ("rounds", C.c_uint64), ("busy_seconds", C.c_double), ("attempts", C.c_ulonglong),
+                ("active", C.c_uint64), ("queued", C.c_uint64), ("mem_used_bytes", C.c_size_t)]
+
+
 # (name, restype, argtypes) of every exported entry point in include/pcpd.h
 SIGNATURES = [
     ("pcpd_create", C.c_void_p, [C.c_uint32, C.c_uint32, C.c_double, C.c_double, C.c_uint64]),
@@ -64,6 +75,14 @@ SIGNATURES = [
     ("pcpd_batch_counts", C.c_int, [C.c_void_p, C.c_size_t, _u64p, C.c_size_t]),
     ("pcpd_batch_lattice", C.c_int, [C.c_void_p, C.c_size_t, _u32p]),
     ("pcpd_batch_destroy", None, [C.c_void_p]),
+    ("pcpd_server_start", C.c_int, [C.POINTER(ServerConfig), C.POINTER(C.c_void_p)]),
+    ("pcpd_server_submit", C.c_int, [C.c_void_p, C.POINTER(Params), C.c_uint64, _u64p, C.c_size_t, C.c_int,
+                                     C.POINTER(C.c_uint64)]),
+    ("pcpd_server_poll", C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(C.c_int)]),
+    ("pcpd_server_result", C.c_int, [C.c_void_p, C.c_uint64, _u64p, C.c_size_t, _u32p, _f64p, _f64p]),
+    ("pcpd_server_wait_idle", C.c_int, [C.c_void_p]),
+    ("pcpd_server_get_stats", C.c_int, [C.c_void_p, C.POINTER(ServerStats)]),
+    ("pcpd_server_stop", None, [C.c_void_p]),
     ("pcpd_sweep_noalloc", C.c_int, [C.c_void_p, C.c_void_p, C.c_uint32, C.c_uint32, C.c_double, C.c_double,
                                      C.c_uint64, C.c_uint64, C.c_uint64, C.c_void_p]),
 ]
@@ -256,6 +275,66 @@ class Batch:
     def __del__(self):
         try:
             self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request loop of the library (pcpd_server_*)."""
+
+    def __init__(self, hbm_budget_bytes: int = 64 << 30, max_active: int = 128,
+                 chunk_attempts: int = 1 << 31, stream=None):
+        cfg = ServerConfig()
+        cfg.hbm_budget_bytes, cfg.max_active, cfg.chunk_attempts = hbm_budget_bytes, max_active, chunk_attempts
+        if stream is not None:
+            cfg.stream = C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+        h = C.c_void_p()
+        _check(load().pcpd_server_start(C.byref(cfg), C.byref(h)))
+        self._h = h
+        self._meta = {}
+
+    def submit(self, L: int, samples: int, p: float, d: float, seed: int, steps_mcs: int,
+               record_times=(), init: int = INIT_FULL, keep_lattice: bool = False) -> int:
+        prm = Params()
+        prm.L, prm.samples, prm.p, prm.d, prm.seed, prm.init = L, samples, p, d, seed, init
+        t = np.ascontiguousarray(record_times, dtype=np.uint64)
+        rid = C.c_uint64()
+        _check(load().pcpd_server_submit(self._h, C.byref(prm), steps_mcs, _ptr(t, C.c_uint64) if t.size else None,
+                                         t.size, 1 if keep_lattice else 0, C.byref(rid)))
+        self._meta[int(rid.value)] = (L, samples, len(t), keep_lattice)
+        return int(rid.value)
+
+    def poll(self, rid: int) -> int:
+        st = C.c_int()
+        _check(load().pcpd_server_poll(self._h, rid, C.byref(st)))
+        return int(st.value)
+
+    def result(self, rid: int):
+        """(counts, lattice or None, latency_s, queue_s) of a request (waits for it)."""
+        L, S, n, keep = self._meta[rid]
+        c = np.zeros(n, dtype=np.uint64)
+        lat = np.zeros((S // 32, L), dtype=np.uint32) if keep else None
+        latency, queue = C.c_double(), C.c_double()
+        _check(load().pcpd_server_result(self._h, rid, _ptr(c, C.c_uint64) if n else None, n,
+                                         _ptr(lat, C.c_uint32) if keep else None, C.byref(latency), C.byref(queue)))
+        return c, lat, latency.value, queue.value
+
+    def wait_idle(self):
+        _check(load().pcpd_server_wait_idle(self._h))
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(load().pcpd_server_get_stats(self._h, C.byref(st)))
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def stop(self):
+        if getattr(self, "_h", None):
+            load().pcpd_server_stop(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.stop()
         except Exception:
             pass
 
