@@ -28,7 +28,8 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_1301_6082_gb300.workloads import SMEM_L65536, log_times  # noqa: E402
+from paper_1301_6082_gb300.replicas import combine, replica_seed  # noqa: E402
+from paper_1301_6082_gb300.workloads import SMEM_L65536, batch_instances, log_times, request_stream  # noqa: E402
 
 METRIC = "attempted site updates/s"
 UNIT = "attempts/s"
@@ -132,6 +133,79 @@ def run_cpu_sample(budget_groups: int = 16, substeps: int = 300):
                       f"from full ({attempts:.3e} attempts, {dt:.1f} s)"}
 
 
+def batch_leg(pcpd, mcs_div: int = 100):
+    """The 512-instance heterogeneous mix (L log-uniform 2^10..2^18, 64/256/1024 samples,
+    d in {.1,...,.9}, p in [.05,.25], MCS log-uniform 1e3..1e5, full or half start, seeds
+    1000+i), with every MCS count divided by mcs_div (declared scale-down; the full mix is
+    ~2.3e14 attempts).  Plain = one engine launch per instance, back to back on one stream;
+    batched = pcpd_batch_run (one persistent launch per 128 instances).  Same results."""
+    import numpy as np
+    import torch
+    mix = batch_instances(512, seed=1)
+    for m in mix:
+        m["mcs_run"] = max(1, m["mcs"] // mcs_div)
+    attempts = sum(m["S"] * (m["L"] // 3) * pcpd.substep_of_time(m["L"], m["mcs_run"]) for m in mix)
+    stream = torch.cuda.Stream()
+    # plain
+    sims = [pcpd.Pcpd(m["L"], m["S"], m["p"], m["d"], seed=m["seed"], init=m["init"], stream=stream) for m in mix]
+    torch.cuda.synchronize()
+    l0 = pcpd.kernel_launches()
+    t0 = time.perf_counter()
+    for s_, m in zip(sims, mix):
+        s_.run(m["mcs_run"], [m["mcs_run"]])
+    stream.synchronize()
+    t_plain = time.perf_counter() - t0
+    plain_launches = pcpd.kernel_launches() - l0
+    plain_counts = [s_.counts()[-1] for s_ in sims]
+    for s_ in sims:
+        s_.close()
+    # batched
+    b = pcpd.Batch(stream=stream)
+    for m in mix:
+        b.add(m["L"], m["S"], m["p"], m["d"], m["seed"], m["mcs_run"], [m["mcs_run"]], init=m["init"])
+    torch.cuda.synchronize()
+    l0 = pcpd.kernel_launches()
+    t0 = time.perf_counter()
+    b.run()
+    t_batch = time.perf_counter() - t0
+    batch_launches = pcpd.kernel_launches() - l0
+    same = all(int(b.counts(i)[-1]) == int(c) for i, c in enumerate(plain_counts))
+    b.close()
+    return {"workload": "512-instance mix, MCS/%d" % mcs_div, "attempts": attempts,
+            "batched": attempts / t_batch, "plain": attempts / t_plain, "unit": UNIT,
+            "speedup": t_plain / t_batch, "batched_launches": batch_launches, "plain_launches": plain_launches,
+            "results_identical": bool(same)}
+
+
+def serving_leg(pcpd, seconds: float = 8.0, mcs_scale: float = 1 / 400, rate_hz: float = 200.0):
+    """Poisson request stream (200 req/s; L log-uniform 2^10..2^20, 64..4096 samples,
+    p in [.05,.25], d in [.1,.9], MCS log-uniform 1e3..1e5) for `seconds` instead of 60 s and
+    with every MCS count scaled by mcs_scale (declared: the stream as specified offers
+    ~7.6e14 attempts/s, hundreds of times one GPU's capacity).  Reports throughput and
+    p50/p99 latency from submission to result."""
+    import numpy as np
+    reqs = request_stream(rate_hz, seconds, seed=1, mcs_scale=mcs_scale)
+    sv = pcpd.Server(hbm_budget_bytes=96 << 30, max_active=128, chunk_attempts=4 << 30)
+    ids = []
+    t0 = time.perf_counter()
+    for r in reqs:
+        wait = r["arrival"] - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        ids.append(sv.submit(r["L"], r["S"], r["p"], r["d"], r["seed"], r["mcs"], [r["mcs"]], init=r["init"]))
+    sv.wait_idle()
+    wall = time.perf_counter() - t0
+    lat = np.array([sv.result(i)[2] for i in ids])
+    st = sv.stats()
+    sv.stop()
+    return {"workload": "Poisson %g req/s for %g s, MCS x %g" % (rate_hz, seconds, mcs_scale),
+            "requests": len(reqs), "completed": int(st["completed"]),
+            "throughput": st["attempts"] / wall, "unit": UNIT,
+            "offered": sum(r["S"] * (r["L"] // 3) * pcpd.substep_of_time(r["L"], r["mcs"]) for r in reqs) / seconds,
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "rounds": int(st["rounds"]), "busy_frac": st["busy_seconds"] / wall}
+
+
 def reference_arm(args, world, rank):
     """The oracle timed on the host cores, one bounded sample of the workload per step."""
     if rank != 0:
@@ -169,6 +243,8 @@ def main():
     ap.add_argument("--mcs-per-step", type=int, default=2000)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -196,7 +272,7 @@ def main():
     stream = torch.cuda.Stream()
     sims = []
     for i, (d, p) in enumerate(runs):
-        sims.append(pcpd.Pcpd(L, S, p, d, seed=W["seed"] + 1000003 * rank, stream=stream))
+        sims.append(pcpd.Pcpd(L, S, p, d, seed=replica_seed(W["seed"], rank), stream=stream))
     ops_item = []
     for d, p in runs:
         td, tda = pcpd.thresholds(p, d)
@@ -235,15 +311,8 @@ def main():
     ms = ev0.elapsed_time(ev1)
     subs = [s.substep - a for s, a in zip(sims, sub0)]
     attempts = sum(S * K_win * n for n in subs)
-    alg_ops = sum(S // 32 * K_win * n * o[0] for n, o in zip(subs, ops_item))
-    if dist:
-        t = torch.tensor([ms, attempts, alg_ops], dtype=torch.float64, device="cuda")
-        tm = t.clone()
-        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        ms_max, attempts_all, alg_all = tm[0].item(), t[1].item(), t[2].item()
-    else:
-        ms_max, attempts_all, alg_all = ms, attempts, alg_ops
+    alg_ops = sum(S // 32 * K_win * n * o[0] for n, o in zip(subs, ops_item))   # this rank
+    (attempts_all,), (ms_max,) = combine(dist, [attempts], [ms], device="cuda")
     value = attempts_all / (ms_max / 1e3)
 
     # roofline of the dominant kernel (the tile sweep): integer issue slots
@@ -259,7 +328,7 @@ def main():
     achieved = (alg_ops / (ms / 1e3)) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                 "frac": achieved / peak, "traffic": None,
-                "kernel": "k_sweep_tile (segmented tiles, tau=128)",
+                "kernel": "k_sweep_persistent (segmented tiles 32768+2x256 sites, tau=128)",
                 "peak_note": f"{sm_count} SMs x 4 SMSPs x 32 lanes x {sm_max_mhz:.0f} MHz issue slots (derived)",
                 "ops_per_attempt": [round(o[0] / 32, 3) for o in ops_item]}
 
@@ -289,14 +358,17 @@ def main():
         dt = time.perf_counter() - t0
         e2e_val = att_e2e / dt
         if dist:
-            t = torch.tensor([dt, att_e2e], dtype=torch.float64, device="cuda")
-            tm = t.clone()
-            dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-            dist.all_reduce(t, op=dist.ReduceOp.SUM)
-            e2e_val = t[1].item() / tm[0].item()
+            (att_all,), (dt_max,) = combine(dist, [att_e2e], [dt], device="cuda")
+            e2e_val = att_all / dt_max
         e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d // args.e2e_steps,
                "d2h_bytes_per_step": d2h // args.e2e_steps,
                "note": "pcpd_set_lattice from pinned host memory + pcpd_run + pcpd_density + pcpd_get_lattice per run per step"}
+
+    for s in sims:
+        s.close()
+    sims = []
+    batch = batch_leg(pcpd) if not args.no_batch else None
+    serving = serving_leg(pcpd) if not args.no_serve else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -314,7 +386,7 @@ def main():
                            "l2": "inputs larger than L2: 3 lattices x 2 buffers x 32 MiB = 192 MiB, streamed per tile epoch",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-                "gpu_launches": launches}
+                "gpu_launches": launches, "batch": batch, "serving": serving}
         print(json.dumps(line), flush=True)
     for s in sims:
         s.close()

@@ -156,6 +156,29 @@ struct pcpd {
 
 namespace {
 
+// The engine's dynamic shared-memory limit is a per-function, process-wide attribute: raise it
+// once to the device maximum for both variants, so that handles with different tile sizes
+// (and threads using them concurrently) never undercut one another.
+std::mutex g_smem_mu;
+bool g_smem_raised = false;
+
+int raise_smem_limit() {
+  std::lock_guard<std::mutex> lock(g_smem_mu);
+  if (g_smem_raised) return PCPD_OK;
+  int optin = 0;
+  int rc = smem_optin(&optin);
+  if (rc) return rc;
+  cudaFuncAttributes fa0, fa1;
+  CU(cudaFuncGetAttributes(&fa0, pcpdk::k_sweep_persistent<false>));
+  CU(cudaFuncGetAttributes(&fa1, pcpdk::k_sweep_persistent<true>));
+  CU(cudaFuncSetAttribute(pcpdk::k_sweep_persistent<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          optin - (int)fa0.sharedSizeBytes));
+  CU(cudaFuncSetAttribute(pcpdk::k_sweep_persistent<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          optin - (int)fa1.sharedSizeBytes));
+  g_smem_raised = true;
+  return PCPD_OK;
+}
+
 // Tile plan.  Columns that fit in shared memory run as RING tiles (whole columns, gpi of them
 // per CTA when they are short, so that a CTA has enough windows per sub-step); longer columns
 // are cut into equal SEGMENT tiles with a halo of 2*tau sites.  No plan changes a result bit.
@@ -218,7 +241,8 @@ int make_plan(pcpd_t *h, const pcpd_params *prm) {
     h->threads = prm->plan_threads;
   }
   h->dyn_smem = 4 * (h->tile_words + list_words);
-  CU(cudaFuncSetAttribute(pcpdk::k_sweep_persistent<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->dyn_smem));
+  rc = raise_smem_limit();
+  if (rc) return rc;
   int per_sm = 0;
   CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcpdk::k_sweep_persistent<false>, (int)h->threads, h->dyn_smem));
   if (per_sm < 1) return fail(PCPD_EINVAL, "tile plan does not fit one CTA per SM");
@@ -879,7 +903,10 @@ int run_multi(cudaStream_t stream, uint32_t *d_ctl, unsigned long long **d_items
     const uint32_t threads = 1024;
     const size_t dyn = 4 * (tile_words + pcpdk::sweep_queue_words(32));
     if (dyn + kStaticSmem > (size_t)optin) return fail(PCPD_EINVAL, "batch tile exceeds shared memory");
-    CU(cudaFuncSetAttribute(pcpdk::k_sweep_persistent<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    {
+      const int rc2 = raise_smem_limit();
+      if (rc2) return rc2;
+    }
     int per_sm = 0;
     CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcpdk::k_sweep_persistent<true>, threads, dyn));
     if (per_sm < 1) return fail(PCPD_EINVAL, "batch plan does not fit one CTA per SM");

@@ -197,3 +197,18 @@ def test_L65536_S4096_sampled_groups(P, oracle_mod, d, p):
 
 def test_L4194304_S1024_sampled_groups(P, oracle_mod):
     _sampled_groups_check(P, oracle_mod, 1 << 22, 1024, 0.15, 0.5, 1, 2, [0, 31])
+
+
+def test_live_handles_with_different_tiles(P):
+    # handles with different tile sizes alive at once (the kernel's shared-memory limit is
+    # process-wide state): create all, then run all, each equal to a lone run
+    spec = [(50000, 32, 0.2, 0.5), (1000, 64, 0.1, 0.3), (20000, 32, 0.15, 0.9), (300, 32, 0.3, 0.1)]
+    sims = [P.Pcpd(L, S, p, d, seed=7 + i, init=INIT_HALF) for i, (L, S, p, d) in enumerate(spec)]
+    for s in sims:
+        s.run(3, [3])
+    for i, ((L, S, p, d), s) in enumerate(zip(spec, sims)):
+        a = P.Pcpd(L, S, p, d, seed=7 + i, init=INIT_HALF)
+        a.run(3, [3])
+        np.testing.assert_array_equal(s.lattice(), a.lattice())
+        a.close()
+        s.close()
