@@ -66,7 +66,8 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.idx = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        import tempfile
+        self.path = os.path.join(tempfile.gettempdir(), f"pcpd_bench_clocks_rank{gpu_index}_{os.getpid()}.csv")
 
     def start(self):
         try:
@@ -327,7 +328,10 @@ def main():
     peak = sm_count * 4 * 32 * sm_max_mhz * 1e6 / 1e12   # T lane-ops/s
     achieved = (alg_ops / (ms / 1e3)) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak,
+                # dram__bytes_read.sum + dram__bytes_write.sum of one bench-size launch (one run,
+                # 2000 MCS = 6001 sub-steps), 1-pass ncu capture; profiles/k_sweep_persistent_L65536_S4096.md
+                "traffic": 38.21e6 + 803.47e6,
                 "kernel": "k_sweep_persistent (segmented tiles 32768+2x256 sites, tau=128)",
                 "peak_note": f"{sm_count} SMs x 4 SMSPs x 32 lanes x {sm_max_mhz:.0f} MHz issue slots (derived)",
                 "ops_per_attempt": [round(o[0] / 32, 3) for o in ops_item]}

@@ -150,6 +150,13 @@ int pcpd_dev_philox(const uint32_t *ctr, uint64_t seed, uint32_t *out, size_t n,
 int pcpd_dev_rate_masks(const uint32_t *words, uint64_t t_d, uint64_t t_da, uint32_t *masks,
                         size_t n, void *stream);
 
+/* Failure-path test: runs the sweep engine on a one-item work list whose predecessor is
+ * never scheduled, with a dependency-wait budget of spin_limit_cycles GPU clock cycles
+ * (1 .. 2^34).  The bounded wait must give up, record the timeout in the engine's error word
+ * and end the CTA; the call then returns PCPD_ETIMEOUT and the CUDA context stays usable.
+ * Any other return code means the failure path did not behave as designed. */
+int pcpd_dev_timeout_test(unsigned long long spin_limit_cycles);
+
 /* ---- batched heterogeneous instances in one persistent launch ----
  * Independent systems run side by side, each with its own seed (the paper runs one system
  * per workgroup, Sec. 3); here any number of instances with different L, samples, p, d,

@@ -1373,3 +1373,65 @@ void pcpd_server_stop(pcpd_server_t *sv) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------------
+// Test entry for the engine's failure path: one item of epoch 1 whose epoch-0 predecessor is
+// never scheduled, so its bounded wait must run out, record kErrDepTimeout and end the CTA.
+// ------------------------------------------------------------------------------------------
+extern "C" int pcpd_dev_timeout_test(unsigned long long spin_limit_cycles) {
+  int rc = device_check();
+  if (rc) return rc;
+  if (spin_limit_cycles == 0 || spin_limit_cycles > (1ull << 34)) return fail(PCPD_EINVAL, "spin limit out of range");
+  pcpd_params prm;
+  memset(&prm, 0, sizeof prm);
+  prm.L = 96;
+  prm.samples = 32;
+  prm.p = 0.1;
+  prm.d = 0.5;
+  prm.seed = 1;
+  prm.plan_tau = 8;
+  pcpd_t *h = nullptr;
+  rc = pcpd_create_ex(&prm, &h);
+  if (rc) return rc;
+  pcpd_batch_t *b = nullptr;
+  rc = pcpd_batch_create(h->stream, &b);
+  if (rc) {
+    pcpd_destroy(h);
+    return rc;
+  }
+  int out = PCPD_OK;
+  {
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    pcpdk::InstDesc D;
+    fill_desc(h, D, 0, 16, 0, 0, 0);
+    const unsigned long long item = pcpdk::pack_item(0, 1, 0);   // epoch 1 of tile 0 only
+    cudaError_t e = cudaMemsetAsync(h->d_done, 0, (h->tiles + 2) * sizeof(uint32_t), h->stream);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof item);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_items, &item, sizeof item, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyToSymbolAsync(pcpdk::c_inst, &D, sizeof D, 0, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_ctl, 0, 2 * sizeof(uint32_t), h->stream);
+    if (e == cudaSuccess) e = (cudaError_t)raise_smem_limit() == 0 ? cudaSuccess : cudaErrorInvalidValue;
+    if (e == cudaSuccess) {
+      pcpdk::BatchParams B;
+      memset(&B, 0, sizeof B);
+      B.items = b->d_items;
+      B.n_items = 1;
+      B.counter = b->d_ctl;
+      B.err = b->d_ctl + 1;
+      B.tile_words = (uint32_t)h->tile_words;
+      B.spin_limit = spin_limit_cycles;
+      pcpdk::k_sweep_persistent<true><<<1, 256, 4 * (h->tile_words + pcpdk::sweep_queue_words(8)), h->stream>>>(B);
+      e = cudaGetLastError();
+    }
+    uint32_t err = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err, b->d_ctl + 1, 4, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) out = fail(PCPD_ECUDA, "timeout test: %s", cudaGetErrorString(e));
+    else if (err == pcpdk::kErrDepTimeout) out = fail(PCPD_ETIMEOUT, "dependency wait gave up after its budget, as designed");
+    else out = fail(PCPD_ESTATE, "timeout test: error word %u, expected %u", err, pcpdk::kErrDepTimeout);
+  }
+  pcpd_batch_destroy(b);
+  pcpd_destroy(h);
+  return out;
+}

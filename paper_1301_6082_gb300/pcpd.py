@@ -68,6 +68,7 @@ SIGNATURES = [
     ("pcpd_substep_of_time", C.c_uint64, [C.c_uint32, C.c_uint64]),
     ("pcpd_dev_philox", C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_size_t, C.c_void_p]),
     ("pcpd_dev_rate_masks", C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_void_p, C.c_size_t, C.c_void_p]),
+    ("pcpd_dev_timeout_test", C.c_int, [C.c_ulonglong]),
     ("pcpd_batch_create", C.c_int, [C.c_void_p, C.POINTER(C.c_void_p)]),
     ("pcpd_batch_add", C.c_int, [C.c_void_p, C.POINTER(Params), C.c_uint64, _u64p, C.c_size_t, C.POINTER(C.c_size_t)]),
     ("pcpd_batch_run", C.c_int, [C.c_void_p]),
@@ -337,6 +338,11 @@ class Server:
             self.stop()
         except Exception:
             pass
+
+
+def dev_timeout_test(spin_limit_cycles: int) -> int:
+    """Return code of the engine's failure-path test (PCPD_ETIMEOUT when it behaves)."""
+    return int(load().pcpd_dev_timeout_test(spin_limit_cycles))
 
 
 def dev_philox(ctr_dev, seed: int, out_dev, n: int, stream=None):

@@ -1,0 +1,34 @@
+"""Failure detection on the GPU without a GPU fault: a dependency flag that nothing sets
+makes the engine's bounded wait give up; the kernel records a timeout code and returns, the
+host reports PCPD_ETIMEOUT, and the context keeps working."""
+import time
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1301_6082_gb300 import build, pcpd
+    build.build()
+    pcpd.load()
+    return pcpd
+
+
+def test_dependency_wait_times_out_and_context_survives(P):
+    t0 = time.perf_counter()
+    rc = P.dev_timeout_test(200_000_000)     # ~0.1 s of GPU clock
+    dt = time.perf_counter() - t0
+    assert rc == P.PCPD_ETIMEOUT, P.load().pcpd_last_error()
+    assert dt < 30.0
+    # the context is still usable: a small run afterwards works and is reproducible
+    a = P.Pcpd(200, 32, 0.15, 0.5, seed=3)
+    a.run(5, [5])
+    b = P.Pcpd(200, 32, 0.15, 0.5, seed=3)
+    b.run(5, [5])
+    np.testing.assert_array_equal(a.lattice(), b.lattice())
