@@ -67,6 +67,8 @@ typedef struct pcpd_params {
     uint32_t plan_threads;   /* threads per CTA (multiple of 32, <= 1024) */
     uint32_t plan_seg_sites; /* core sites per tile for lattices that do not fit one CTA */
     uint32_t plan_tau;       /* sub-steps per tile residency (temporal block) */
+    int autotune;            /* non-zero and no plan_* override: use the plan pcpd_autotune
+                                picks for this (L, samples), tuning on first use */
 } pcpd_params;
 
 /* Create a simulation of `samples` PCPD samples on a ring of L sites, initialised fully
@@ -149,6 +151,16 @@ int pcpd_dev_philox(const uint32_t *ctr, uint64_t seed, uint32_t *out, size_t n,
  * using the early-exit MSB-first compare of the sweep kernels. */
 int pcpd_dev_rate_masks(const uint32_t *words, uint64_t t_d, uint64_t t_da, uint32_t *masks,
                         size_t n, void *stream);
+
+/* Autotuner: time candidate tile plans (threads per CTA -- i.e. windows per thread --, the
+ * temporal block tau, the tile size and so the shared-memory residency) on trial_substeps
+ * sub-steps of the instance prm describes, and return in *best (a copy of *prm with the
+ * plan_* fields set) the fastest, with its rate in attempted updates/s (nullable).  Every
+ * plan gives bit-identical results, so the choice only affects speed.  The winner is cached
+ * per (L, samples) in the process and, if the environment variable PCPD_TUNE_CACHE names a
+ * file, appended to it and read back by later processes.  Allocates and frees trial handles. */
+int pcpd_autotune(const pcpd_params *prm, uint32_t trial_substeps, pcpd_params *best,
+                  double *best_rate);
 
 /* Failure-path test: runs the sweep engine on a one-item work list whose predecessor is
  * never scheduled, with a dependency-wait budget of spin_limit_cycles GPU clock cycles

@@ -11,6 +11,7 @@
 #include <chrono>
 #include <condition_variable>
 #include <deque>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <thread>
@@ -320,6 +321,8 @@ void fill_desc(const pcpd_t *h, pcpdk::InstDesc &D, uint64_t n_begin, uint64_t n
   D.T = h->T;
 }
 
+int tuned_plan(const pcpd_params *prm, pcpd_params *out);
+
 // The error word of the engine: 0, or a device-side wait that ran out of its budget.
 int check_engine(const pcpd_t *h) {
   uint32_t err = 0;
@@ -418,6 +421,12 @@ int pcpd_create_ex(const pcpd_params *prm, pcpd_t **out) {
   rc = device_check();
   if (rc) return rc;
 
+  pcpd_params tuned;
+  if (prm->autotune && !prm->plan_threads && !prm->plan_seg_sites && !prm->plan_tau) {
+    rc = tuned_plan(prm, &tuned);
+    if (rc) return rc;
+    prm = &tuned;
+  }
   pcpd_t *h = new pcpd();
   h->L = prm->L;
   h->K = prm->L / 3u;
@@ -1434,4 +1443,146 @@ extern "C" int pcpd_dev_timeout_test(unsigned long long spin_limit_cycles) {
   pcpd_batch_destroy(b);
   pcpd_destroy(h);
   return out;
+}
+
+// ------------------------------------------------------------------------------------------
+// Autotuner: time candidate plans on the real instance and keep the fastest.
+// ------------------------------------------------------------------------------------------
+namespace {
+
+struct TunedPlan {
+  uint32_t threads, seg, tau;
+  double rate;
+};
+std::mutex g_tune_mu;
+std::map<std::pair<uint32_t, uint32_t>, TunedPlan> g_tune;
+bool g_tune_file_read = false;
+
+void tune_file_load() {
+  if (g_tune_file_read) return;
+  g_tune_file_read = true;
+  const char *path = getenv("PCPD_TUNE_CACHE");
+  if (!path) return;
+  FILE *f = fopen(path, "r");
+  if (!f) return;
+  unsigned L, S, th, seg, tau;
+  double rate;
+  while (fscanf(f, "%u %u %u %u %u %lf", &L, &S, &th, &seg, &tau, &rate) == 6) g_tune[{L, S}] = {th, seg, tau, rate};
+  fclose(f);
+}
+
+void tune_file_append(uint32_t L, uint32_t S, const TunedPlan &t) {
+  const char *path = getenv("PCPD_TUNE_CACHE");
+  if (!path) return;
+  FILE *f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "%u %u %u %u %u %.6e\n", L, S, t.threads, t.seg, t.tau, t.rate);
+  fclose(f);
+}
+
+// Rate of one plan: attempted updates/s over trial sub-steps after one warm-up epoch.
+int time_plan(const pcpd_params *prm, uint32_t trial, double *rate) {
+  pcpd_params p2 = *prm;
+  p2.autotune = 0;
+  p2.per_sample = 0;
+  p2.stream = nullptr;
+  p2.dev_lattice = nullptr;
+  pcpd_t *h = nullptr;
+  int rc = pcpd_create_ex(&p2, &h);
+  if (rc) return rc;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  rc = pcpd_run_substeps(h, std::min<uint64_t>(trial, h->tau));
+  if (rc == PCPD_OK) rc = pcpd_sync(h);
+  if (rc == PCPD_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+    rc = fail(PCPD_ECUDA, "event create");
+  float ms = 0.f;
+  if (rc == PCPD_OK) {
+    cudaEventRecord(e0, h->stream);
+    rc = pcpd_run_substeps(h, trial);
+    cudaEventRecord(e1, h->stream);
+    if (rc == PCPD_OK) rc = pcpd_sync(h);
+    if (rc == PCPD_OK) cudaEventElapsedTime(&ms, e0, e1);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (rc == PCPD_OK) *rate = ms > 0.f ? (double)h->S * h->K * trial / (ms * 1e-3) : 0.0;
+  pcpd_destroy(h);
+  return rc;
+}
+
+int tuned_plan(const pcpd_params *prm, pcpd_params *out) {
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    tune_file_load();
+    auto it = g_tune.find({prm->L, prm->samples});
+    if (it != g_tune.end()) {
+      *out = *prm;
+      out->autotune = 0;
+      out->plan_threads = it->second.threads;
+      out->plan_seg_sites = it->second.seg;
+      out->plan_tau = it->second.tau;
+      return PCPD_OK;
+    }
+  }
+  return pcpd_autotune(prm, 0, out, nullptr);
+}
+
+}  // namespace
+
+extern "C" int pcpd_autotune(const pcpd_params *prm, uint32_t trial_substeps, pcpd_params *best, double *best_rate) {
+  if (!prm || !best) return fail(PCPD_EINVAL, "NULL argument");
+  int rc = device_check();
+  if (rc) return rc;
+  // the default plan tells RING from SEGMENT and gives the largest tile
+  pcpd base;
+  base.L = prm->L;
+  base.K = prm->L / 3u;
+  base.S = prm->samples;
+  base.G = prm->samples / 32u;
+  if (prm->samples == 0 || prm->samples % 32 || prm->L < 3) return fail(PCPD_EINVAL, "bad L or samples");
+  rc = make_plan(&base, nullptr);
+  if (rc) return rc;
+  struct Cand {
+    uint32_t threads, seg, tau;
+  };
+  std::vector<Cand> cands;
+  if (base.ring) {
+    for (uint32_t th : {256u, 512u, 1024u})
+      if (th <= 1024u && (th <= base.threads * 2u || th == 256u)) cands.push_back({th, 0u, 0u});
+  } else {
+    const uint32_t half = ((base.core / 2u) + 3u) & ~3u;
+    for (uint32_t th : {512u, 1024u})
+      for (uint32_t tau : {64u, 128u, 256u})
+        for (uint32_t seg : {base.core, half}) {
+          if (seg + 4u * tau + 12u > prm->L || (prm->L + seg - 1) / seg < 2) continue;
+          cands.push_back({th, seg, tau});
+        }
+  }
+  if (trial_substeps == 0) trial_substeps = base.ring ? 256u : 512u;
+  double best_r = -1.0;
+  Cand win{0, 0, 0};
+  for (const Cand &c : cands) {
+    pcpd_params p2 = *prm;
+    p2.plan_threads = c.threads;
+    p2.plan_seg_sites = c.seg;
+    p2.plan_tau = c.tau;
+    double r = 0.0;
+    if (time_plan(&p2, trial_substeps, &r) != PCPD_OK) continue;   // a plan that does not fit is skipped
+    if (r > best_r) {
+      best_r = r;
+      win = c;
+    }
+  }
+  if (best_r < 0.0) return fail(PCPD_EINVAL, "no candidate plan could run");
+  *best = *prm;
+  best->autotune = 0;
+  best->plan_threads = win.threads;
+  best->plan_seg_sites = win.seg;
+  best->plan_tau = win.tau;
+  if (best_rate) *best_rate = best_r;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  const TunedPlan t{win.threads, win.seg, win.tau, best_r};
+  g_tune[{prm->L, prm->samples}] = t;
+  tune_file_append(prm->L, prm->samples, t);
+  return PCPD_OK;
 }

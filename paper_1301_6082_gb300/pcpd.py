@@ -32,7 +32,8 @@ class Params(C.Structure):
     _fields_ = [("L", C.c_uint32), ("samples", C.c_uint32), ("p", C.c_double), ("d", C.c_double),
                 ("seed", C.c_uint64), ("init", C.c_int), ("stream", C.c_void_p),
                 ("dev_lattice", C.c_void_p), ("dev_bytes", C.c_size_t), ("per_sample", C.c_int),
-                ("plan_threads", C.c_uint32), ("plan_seg_sites", C.c_uint32), ("plan_tau", C.c_uint32)]
+                ("plan_threads", C.c_uint32), ("plan_seg_sites", C.c_uint32), ("plan_tau", C.c_uint32),
+                ("autotune", C.c_int)]
 
 
 class ServerConfig(C.Structure):
@@ -69,6 +70,7 @@ SIGNATURES = [
     ("pcpd_dev_philox", C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_size_t, C.c_void_p]),
     ("pcpd_dev_rate_masks", C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_void_p, C.c_size_t, C.c_void_p]),
     ("pcpd_dev_timeout_test", C.c_int, [C.c_ulonglong]),
+    ("pcpd_autotune", C.c_int, [C.POINTER(Params), C.c_uint32, C.POINTER(Params), _f64p]),
     ("pcpd_batch_create", C.c_int, [C.c_void_p, C.POINTER(C.c_void_p)]),
     ("pcpd_batch_add", C.c_int, [C.c_void_p, C.POINTER(Params), C.c_uint64, _u64p, C.c_size_t, C.POINTER(C.c_size_t)]),
     ("pcpd_batch_run", C.c_int, [C.c_void_p]),
@@ -135,12 +137,13 @@ class Pcpd:
     def __init__(self, L: int, samples: int, p: float, d: float, seed: int = 1,
                  init: int = INIT_FULL, per_sample: bool = False, stream=None,
                  dev_lattice=None, plan_threads: int = 0, plan_seg_sites: int = 0,
-                 plan_tau: int = 0):
+                 plan_tau: int = 0, autotune: bool = False):
         lib = load()
         prm = Params()
         prm.L, prm.samples, prm.p, prm.d, prm.seed, prm.init = L, samples, p, d, seed, init
         prm.per_sample = 1 if per_sample else 0
         prm.plan_threads, prm.plan_seg_sites, prm.plan_tau = plan_threads, plan_seg_sites, plan_tau
+        prm.autotune = 1 if autotune else 0
         if stream is not None:
             prm.stream = C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
         self._keep = dev_lattice
@@ -338,6 +341,17 @@ class Server:
             self.stop()
         except Exception:
             pass
+
+
+def autotune(L: int, samples: int, p: float, d: float, seed: int = 1, trial_substeps: int = 0):
+    """Fastest plan for (L, samples): dict(plan_threads, plan_seg_sites, plan_tau, rate)."""
+    prm = Params()
+    prm.L, prm.samples, prm.p, prm.d, prm.seed = L, samples, p, d, seed
+    best = Params()
+    rate = C.c_double()
+    _check(load().pcpd_autotune(C.byref(prm), trial_substeps, C.byref(best), C.byref(rate)))
+    return {"plan_threads": best.plan_threads, "plan_seg_sites": best.plan_seg_sites,
+            "plan_tau": best.plan_tau, "rate": rate.value}
 
 
 def dev_timeout_test(spin_limit_cycles: int) -> int:
