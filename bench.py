@@ -178,6 +178,35 @@ def batch_leg(pcpd, mcs_div: int = 100):
             "results_identical": bool(same)}
 
 
+def stream_leg(pcpd, substeps: int = 2048):
+    """The HBM-streamed workload: L = 2^22 sites, 1024 samples, d=0.5, p=0.15, full start,
+    seed 1 (the lattice, 2 x 512 MiB, is far larger than shared memory and L2, so every
+    epoch of tau sub-steps streams each tile in with its halo and its core back out).
+    Times `substeps` sub-steps after one warm-up epoch; HBM bytes are the algorithmic tile
+    traffic (tile with halo read + core written, per epoch)."""
+    import torch
+    L, S = 1 << 22, 1024
+    stream = torch.cuda.Stream()
+    sim = pcpd.Pcpd(L, S, 0.15, 0.5, seed=1, stream=stream)
+    sim.run_substeps(256)
+    sim.sync()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    sim.run_substeps(substeps)
+    ev1.record(stream)
+    sim.sync()
+    ms = ev0.elapsed_time(ev1)
+    plan = sim.plan()
+    epochs = -(-substeps // plan["tau"])
+    G = S // 32
+    tile_bytes = G * (L + plan["n_seg"] * 2 * plan["halo"]) * 4 + G * L * 4
+    hbm = tile_bytes * epochs / (ms / 1e3) / 1e9
+    sim.close()
+    return {"workload": "L=2^22, 1024 samples, d=0.5, p=0.15, %d sub-steps" % substeps,
+            "value": S * (L // 3) * substeps / (ms / 1e3), "unit": UNIT, "plan": plan,
+            "hbm_gbs_algorithmic": hbm, "hbm_frac_of_measured_copy": hbm / 6787.2}
+
+
 def serving_leg(pcpd, seconds: float = 8.0, mcs_scale: float = 1 / 400, rate_hz: float = 200.0):
     """Poisson request stream (200 req/s; L log-uniform 2^10..2^20, 64..4096 samples,
     p in [.05,.25], d in [.1,.9], MCS log-uniform 1e3..1e5) for `seconds` instead of 60 s and
@@ -246,6 +275,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-stream", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -373,6 +403,7 @@ def main():
     sims = []
     batch = batch_leg(pcpd) if not args.no_batch else None
     serving = serving_leg(pcpd) if not args.no_serve else None
+    streamed = stream_leg(pcpd) if not args.no_stream else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -390,7 +421,7 @@ def main():
                            "l2": "inputs larger than L2: 3 lattices x 2 buffers x 32 MiB = 192 MiB, streamed per tile epoch",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-                "gpu_launches": launches, "batch": batch, "serving": serving}
+                "gpu_launches": launches, "batch": batch, "serving": serving, "streamed": streamed}
         print(json.dumps(line), flush=True)
     for s in sims:
         s.close()

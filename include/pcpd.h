@@ -118,6 +118,23 @@ int pcpd_run_substeps(pcpd_t *h, uint64_t n_substeps);
 uint64_t pcpd_substep(const pcpd_t *h);
 uint64_t pcpd_time_mcs(const pcpd_t *h);
 
+/* The tile plan a handle runs with (see pcpd_params.plan_*). */
+typedef struct pcpd_plan_info {
+    uint32_t ring;       /* 1: tiles are whole columns (shared-memory resident for the run) */
+    uint32_t gpi;        /* columns per tile (RING) */
+    uint32_t threads;    /* threads per CTA */
+    uint32_t core;       /* core sites per tile */
+    uint32_t halo;       /* halo sites per side (SEGMENT; 2*tau) */
+    uint32_t tau;        /* sub-steps per tile residency */
+    uint32_t n_seg;      /* tiles per column */
+    uint32_t tiles;      /* tiles per epoch */
+    uint32_t grid;       /* persistent CTAs */
+    uint32_t pad_;
+    size_t smem_bytes;   /* dynamic shared memory per CTA */
+} pcpd_plan_info;
+
+int pcpd_get_plan(const pcpd_t *h, pcpd_plan_info *out);
+
 /* Block until all work enqueued for the handle has finished. */
 int pcpd_sync(pcpd_t *h);
 

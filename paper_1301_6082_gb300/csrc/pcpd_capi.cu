@@ -565,6 +565,22 @@ int pcpd_run_substeps(pcpd_t *h, uint64_t n_substeps) {
 
 size_t pcpd_num_records(const pcpd_t *h) { return h ? h->rec_times.size() : 0; }
 
+int pcpd_get_plan(const pcpd_t *h, pcpd_plan_info *out) {
+  if (!h || !out) return fail(PCPD_EINVAL, "NULL argument");
+  memset(out, 0, sizeof *out);
+  out->ring = h->ring ? 1u : 0u;
+  out->gpi = h->gpi;
+  out->threads = h->threads;
+  out->core = h->core;
+  out->halo = h->halo;
+  out->tau = h->tau;
+  out->n_seg = h->n_seg;
+  out->tiles = h->tiles;
+  out->grid = (uint32_t)h->grid;
+  out->smem_bytes = h->dyn_smem;
+  return PCPD_OK;
+}
+
 uint64_t pcpd_substep(const pcpd_t *h) { return h ? h->n_now : 0; }
 uint64_t pcpd_time_mcs(const pcpd_t *h) { return h ? h->t_now : 0; }
 
@@ -794,6 +810,24 @@ extern "C" int pcpd_sweep_noalloc(uint32_t *lat_in, uint32_t *lat_out, uint32_t 
 // Batches: many instances (any L, samples, p, d, seed, step count, records) in one persistent
 // launch of the engine over an explicit item list.
 // ------------------------------------------------------------------------------------------
+namespace {
+// A batch round as a CUDA graph: the item-list and descriptor uploads (from pinned staging
+// buffers), the counter reset and the engine launch, captured once and updated in place
+// (cudaGraphExecUpdate) for later rounds of the same shape.
+struct GraphCache {
+  cudaGraphExec_t exec = nullptr;
+  unsigned long long *h_items = nullptr;   // pinned
+  size_t h_items_cap = 0;
+  pcpdk::InstDesc *h_desc = nullptr;       // pinned, kMaxBatchInst entries
+  ~GraphCache() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (h_items) cudaFreeHost(h_items);
+    if (h_desc) cudaFreeHost(h_desc);
+  }
+};
+
+}  // namespace
+
 struct pcpd_batch {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -804,6 +838,7 @@ struct pcpd_batch {
   size_t items_cap = 0;
   uint32_t *d_ctl = nullptr;   // work counter, error word
   bool ran = false;
+  GraphCache gc;
 };
 
 namespace {
@@ -825,7 +860,7 @@ struct MultiTarget {
 // list starts every segmented chain at once and spreads the whole-ring items (longest first)
 // between its epochs.  Waits for completion; updates each handle's buffer and clock.
 int run_multi(cudaStream_t stream, uint32_t *d_ctl, unsigned long long **d_items, size_t *items_cap,
-              std::vector<MultiTarget> &tg) {
+              std::vector<MultiTarget> &tg, GraphCache &gc) {
   int dev = 0, sms = 0, optin = 0;
   CU(cudaGetDevice(&dev));
   CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -896,11 +931,16 @@ int run_multi(cudaStream_t stream, uint32_t *d_ctl, unsigned long long **d_items
       CU(cudaMalloc(d_items, items.size() * sizeof(unsigned long long)));
       *items_cap = items.size();
     }
-    CU(cudaMemcpyAsync(*d_items, items.data(), items.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice,
-                       stream));
-    CU(cudaMemcpyToSymbolAsync(pcpdk::c_inst, desc.data(), desc.size() * sizeof(pcpdk::InstDesc), 0,
-                               cudaMemcpyHostToDevice, stream));
-    CU(cudaMemsetAsync(d_ctl, 0, sizeof(uint32_t), stream));   // work counter
+    if (items.size() > gc.h_items_cap) {
+      CU(cudaStreamSynchronize(stream));
+      if (gc.h_items) cudaFreeHost(gc.h_items);
+      gc.h_items = nullptr;
+      CU(cudaMallocHost(&gc.h_items, items.size() * sizeof(unsigned long long)));
+      gc.h_items_cap = items.size();
+    }
+    if (!gc.h_desc) CU(cudaMallocHost(&gc.h_desc, pcpdk::kMaxBatchInst * sizeof(pcpdk::InstDesc)));
+    memcpy(gc.h_items, items.data(), items.size() * sizeof(unsigned long long));
+    memcpy(gc.h_desc, desc.data(), desc.size() * sizeof(pcpdk::InstDesc));
     pcpdk::BatchParams B;
     memset(&B, 0, sizeof B);
     B.items = *d_items;
@@ -920,8 +960,39 @@ int run_multi(cudaStream_t stream, uint32_t *d_ctl, unsigned long long **d_items
     CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcpdk::k_sweep_persistent<true>, threads, dyn));
     if (per_sm < 1) return fail(PCPD_EINVAL, "batch plan does not fit one CTA per SM");
     const int grid = (int)std::min<uint64_t>((uint64_t)per_sm * sms, items.size());
+    // capture the round, then update the cached executable graph (or instantiate it)
+    CU(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+    cudaMemcpyAsync(*d_items, gc.h_items, items.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice, stream);
+    cudaMemcpyToSymbolAsync(pcpdk::c_inst, gc.h_desc, desc.size() * sizeof(pcpdk::InstDesc), 0,
+                            cudaMemcpyHostToDevice, stream);
+    cudaMemsetAsync(d_ctl, 0, sizeof(uint32_t), stream);   // work counter
     pcpdk::k_sweep_persistent<true><<<grid, threads, dyn, stream>>>(B);
-    CU(cudaGetLastError());
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(stream, &graph);
+    if (ec != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return fail(PCPD_ECUDA, "graph capture: %s", cudaGetErrorString(ec));
+    }
+    bool updated = false;
+    if (gc.exec) {
+      cudaGraphExecUpdateResultInfo info;
+      updated = cudaGraphExecUpdate(gc.exec, graph, &info) == cudaSuccess;
+      if (!updated) {
+        cudaGetLastError();
+        cudaGraphExecDestroy(gc.exec);
+        gc.exec = nullptr;
+      }
+    }
+    if (!updated) {
+      const cudaError_t ei = cudaGraphInstantiate(&gc.exec, graph, 0);
+      if (ei != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        gc.exec = nullptr;
+        return fail(PCPD_ECUDA, "graph instantiate: %s", cudaGetErrorString(ei));
+      }
+    }
+    cudaGraphDestroy(graph);
+    CU(cudaGraphLaunch(gc.exec, stream));
     g_launches.fetch_add(1, std::memory_order_relaxed);
     // the next launch rewrites the constant table and the host vectors go out of scope
     CU(cudaStreamSynchronize(stream));
@@ -1027,7 +1098,7 @@ int pcpd_batch_run(pcpd_batch_t *b) {
     tg[i].rec_first = 0;
     tg[i].slot0 = 0;
   }
-  int rc = run_multi(b->stream, b->d_ctl, &b->d_items, &b->items_cap, tg);
+  int rc = run_multi(b->stream, b->d_ctl, &b->d_items, &b->items_cap, tg, b->gc);
   if (rc) return rc;
   for (size_t i = 0; i < n; ++i) {
     pcpd_t *h = b->inst[i];
@@ -1096,6 +1167,7 @@ struct pcpd_server {
   uint32_t *d_ctl = nullptr;
   unsigned long long *d_items = nullptr;
   size_t items_cap = 0;
+  GraphCache gc;
   std::thread th;
   std::mutex mu;
   std::condition_variable cv, cv_done;
@@ -1209,7 +1281,7 @@ void server_loop(pcpd_server_t *sv) {
       round_attempts += per_sub * (tg[i].n_end - h->n_now);
     }
     const Clock::time_point t0 = Clock::now();
-    const int rc = run_multi(sv->stream, sv->d_ctl, &sv->d_items, &sv->items_cap, tg);
+    const int rc = run_multi(sv->stream, sv->d_ctl, &sv->d_items, &sv->items_cap, tg, sv->gc);
     const double dt = std::chrono::duration<double>(Clock::now() - t0).count();
     {
       std::lock_guard<std::mutex> lock(sv->mu);

@@ -36,6 +36,12 @@ class Params(C.Structure):
                 ("autotune", C.c_int)]
 
 
+class PlanInfo(C.Structure):
+    _fields_ = [("ring", C.c_uint32), ("gpi", C.c_uint32), ("threads", C.c_uint32), ("core", C.c_uint32),
+                ("halo", C.c_uint32), ("tau", C.c_uint32), ("n_seg", C.c_uint32), ("tiles", C.c_uint32),
+                ("grid", C.c_uint32), ("pad_", C.c_uint32), ("smem_bytes", C.c_size_t)]
+
+
 class ServerConfig(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_active", C.c_uint32), ("chunk_attempts", C.c_uint64),
                 ("stream", C.c_void_p)]
@@ -53,6 +59,7 @@ SIGNATURES = [
     ("pcpd_create_ex", C.c_int, [C.POINTER(Params), C.POINTER(C.c_void_p)]),
     ("pcpd_run", C.c_int, [C.c_void_p, C.c_uint64, _u64p, C.c_size_t]),
     ("pcpd_num_records", C.c_size_t, [C.c_void_p]),
+    ("pcpd_get_plan", C.c_int, [C.c_void_p, C.POINTER(PlanInfo)]),
     ("pcpd_density", C.c_int, [C.c_void_p, _f64p, _u64p, C.c_size_t]),
     ("pcpd_record_times", C.c_int, [C.c_void_p, _u64p, C.c_size_t]),
     ("pcpd_sample_counts", C.c_int, [C.c_void_p, C.c_size_t, _u32p]),
@@ -230,6 +237,11 @@ class Pcpd:
 
     def sync(self):
         _check(load().pcpd_sync(self._h))
+
+    def plan(self) -> dict:
+        info = PlanInfo()
+        _check(load().pcpd_get_plan(self._h, C.byref(info)))
+        return {f: getattr(info, f) for f, _ in PlanInfo._fields_ if f != "pad_"}
 
 
 class Batch:
