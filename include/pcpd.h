@@ -69,6 +69,9 @@ typedef struct pcpd_params {
     uint32_t plan_tau;       /* sub-steps per tile residency (temporal block) */
     int autotune;            /* non-zero and no plan_* override: use the plan pcpd_autotune
                                 picks for this (L, samples), tuning on first use */
+    int jit;                 /* specialise the sweep for this instance's two thresholds by
+                                compiling it at run time (same bits, ~15% faster): 1 = yes,
+                                -1 = no, 0 = automatically for lattices of >= 2^22 words */
 } pcpd_params;
 
 /* Create a simulation of `samples` PCPD samples on a ring of L sites, initialised fully
@@ -129,7 +132,7 @@ typedef struct pcpd_plan_info {
     uint32_t n_seg;      /* tiles per column */
     uint32_t tiles;      /* tiles per epoch */
     uint32_t grid;       /* persistent CTAs */
-    uint32_t pad_;
+    uint32_t jit;        /* 1: runs a sweep compiled for this instance's thresholds */
     size_t smem_bytes;   /* dynamic shared memory per CTA */
 } pcpd_plan_info;
 

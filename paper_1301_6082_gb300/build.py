@@ -10,7 +10,41 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libpcpd.so")
 SOURCES = [os.path.join(CSRC, "pcpd_capi.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, "pcpd_kernels.cuh"), os.path.join(CSRC, "pcpd_engine.cuh"),
+                  os.path.join(CSRC, "pcpd_jit_src.inc"),
                   os.path.join(os.path.dirname(HERE), "include", "pcpd.h")]
+
+
+JIT_SRC = os.path.join(CSRC, "pcpd_jit_src.inc")
+JIT_PRELUDE = """// runtime-compiled copy of the sweep engine (generated by build.py; do not edit)
+#define PCPD_JIT_SOURCE 1
+typedef unsigned int uint32_t;
+typedef int int32_t;
+typedef unsigned long long uint64_t;
+typedef long long int64_t;
+typedef unsigned long long uintptr_t;
+"""
+JIT_ENTRY = """
+extern "C" __global__ void __launch_bounds__(1024, 1) pcpd_jit_sweep(const pcpdk::BatchParams B) {
+  pcpdk::sweep_body<false>(B);
+}
+"""
+
+
+def write_jit_source() -> str:
+    """The engine's source as a C string for the runtime compiler (thresholds as constants)."""
+    parts = [JIT_PRELUDE]
+    for fn in ("pcpd_kernels.cuh", "pcpd_engine.cuh"):
+        parts.append(open(os.path.join(CSRC, fn)).read())
+    parts.append(JIT_ENTRY)
+    body = "\n".join(parts)
+    assert ")PCPDJIT\"" not in body
+    text = "// generated by build.py from pcpd_kernels.cuh and pcpd_engine.cuh\n" \
+           "static const char kJitSource[] = R\"PCPDJIT(" + body + ")PCPDJIT\";\n"
+    old = open(JIT_SRC).read() if os.path.exists(JIT_SRC) else None
+    if old != text:
+        with open(JIT_SRC, "w") as f:
+            f.write(text)
+    return JIT_SRC
 
 
 def nvcc() -> str:
@@ -26,11 +60,12 @@ def flags(extra=()):
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
+    write_jit_source()
     stale = force or not os.path.exists(LIB) or any(
         os.path.getmtime(d) > os.path.getmtime(LIB) for d in DEPS)
     if stale:
         tmp = LIB + ".tmp%d" % os.getpid()
-        cmd = [nvcc(), *flags(["-Xptxas", "-v"] if verbose else []), *SOURCES, "-o", tmp, "-lcudart"]
+        cmd = [nvcc(), *flags(["-Xptxas", "-v"] if verbose else []), *SOURCES, "-o", tmp, "-lcudart", "-ldl"]
         subprocess.check_call(cmd)
         os.replace(tmp, LIB)
     return LIB

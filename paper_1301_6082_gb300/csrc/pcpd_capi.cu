@@ -1,6 +1,11 @@
 // pcpd_capi.cu -- the C ABI of libpcpd.so (declared in include/pcpd.h): handles, thresholds,
 // time bookkeeping, tile plans and kernel launches for the bit-sliced PCPD sweep.
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <dlfcn.h>
+#include <nvrtc.h>
+
+#include <type_traits>
 
 #include <atomic>
 #include <cmath>
@@ -12,6 +17,7 @@
 #include <condition_variable>
 #include <deque>
 #include <map>
+#include <tuple>
 #include <memory>
 #include <mutex>
 #include <thread>
@@ -153,6 +159,7 @@ struct pcpd {
   // engine scratch: per-tile epoch flags, work counter, error word
   uint32_t *d_done = nullptr;   // [tiles], then counter, then error word
   uint32_t tiles = 0;
+  CUfunction jit_fn = nullptr;  // sweep compiled for this instance's thresholds, or null
 };
 
 namespace {
@@ -177,6 +184,124 @@ int raise_smem_limit() {
   CU(cudaFuncSetAttribute(pcpdk::k_sweep_persistent<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           optin - (int)fa1.sharedSizeBytes));
   g_smem_raised = true;
+  return PCPD_OK;
+}
+
+// ---- sweep specialised for one (T_D, T_DA) pair, compiled at run time ----
+#include "pcpd_jit_src.inc"
+
+// The runtime compiler and the driver calls it needs, resolved at run time so that the
+// library loads (and the generic kernels run) even where either is missing.
+struct JitApi {
+  bool ok = false;
+  nvrtcResult (*create)(nvrtcProgram *, const char *, const char *, int, const char *const *, const char *const *);
+  nvrtcResult (*compile)(nvrtcProgram, int, const char *const *);
+  nvrtcResult (*log_size)(nvrtcProgram, size_t *);
+  nvrtcResult (*log)(nvrtcProgram, char *);
+  nvrtcResult (*cubin_size)(nvrtcProgram, size_t *);
+  nvrtcResult (*cubin)(nvrtcProgram, char *);
+  nvrtcResult (*destroy)(nvrtcProgram *);
+  CUresult (*load)(CUmodule *, const void *);
+  CUresult (*get_fn)(CUfunction *, CUmodule, const char *);
+  CUresult (*get_attr)(int *, CUfunction_attribute, CUfunction);
+  CUresult (*set_attr)(CUfunction, CUfunction_attribute, int);
+  CUresult (*occupancy)(int *, CUfunction, int, size_t);
+  CUresult (*launch)(CUfunction, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned, CUstream,
+                     void **, void **);
+};
+
+std::mutex g_jit_mu;
+JitApi g_jit_api;
+bool g_jit_api_tried = false;
+std::map<std::tuple<int, uint32_t, uint32_t>, CUfunction> g_jit;
+
+template <typename F>
+bool driver_fn(const char *name, F *out) {
+  cudaDriverEntryPointQueryResult st;
+  void *p = nullptr;
+  if (cudaGetDriverEntryPointByVersion(name, &p, 12000, cudaEnableDefault, &st) != cudaSuccess ||
+      st != cudaDriverEntryPointSuccess || !p)
+    return false;
+  *out = reinterpret_cast<F>(p);
+  return true;
+}
+
+const JitApi &jit_api() {   // call with g_jit_mu held
+  if (g_jit_api_tried) return g_jit_api;
+  g_jit_api_tried = true;
+  JitApi a;
+  void *lib = dlopen("libnvrtc.so.13", RTLD_NOW | RTLD_LOCAL);
+  if (!lib) lib = dlopen("libnvrtc.so", RTLD_NOW | RTLD_LOCAL);
+  if (!lib) return g_jit_api;
+  bool ok = true;
+  auto sym = [&](const char *n, auto *f) {
+    void *p = dlsym(lib, n);
+    ok = ok && p;
+    *f = reinterpret_cast<std::remove_pointer_t<decltype(f)>>(p);
+  };
+  sym("nvrtcCreateProgram", &a.create);
+  sym("nvrtcCompileProgram", &a.compile);
+  sym("nvrtcGetProgramLogSize", &a.log_size);
+  sym("nvrtcGetProgramLog", &a.log);
+  sym("nvrtcGetCUBINSize", &a.cubin_size);
+  sym("nvrtcGetCUBIN", &a.cubin);
+  sym("nvrtcDestroyProgram", &a.destroy);
+  ok = ok && driver_fn("cuModuleLoadData", &a.load) && driver_fn("cuModuleGetFunction", &a.get_fn) &&
+       driver_fn("cuFuncGetAttribute", &a.get_attr) && driver_fn("cuFuncSetAttribute", &a.set_attr) &&
+       driver_fn("cuOccupancyMaxActiveBlocksPerMultiprocessor", &a.occupancy) &&
+       driver_fn("cuLaunchKernel", &a.launch);
+  a.ok = ok;
+  g_jit_api = a;
+  return g_jit_api;
+}
+
+// Compile (once per device and threshold pair) the engine with both thresholds as constants.
+int jit_function(uint32_t td, uint32_t tda, CUfunction *out) {
+  int dev = 0;
+  CU(cudaGetDevice(&dev));
+  CU(cudaFree(nullptr));   // the runtime's primary context is current for the driver calls
+  std::lock_guard<std::mutex> lock(g_jit_mu);
+  const JitApi &J = jit_api();
+  if (!J.ok) return fail(PCPD_ECUDA, "runtime compiler or driver entry points unavailable");
+  auto key = std::make_tuple(dev, td, tda);
+  auto it = g_jit.find(key);
+  if (it != g_jit.end()) {
+    *out = it->second;
+    return PCPD_OK;
+  }
+  nvrtcProgram prog;
+  if (J.create(&prog, kJitSource, "pcpd_jit.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS)
+    return fail(PCPD_ECUDA, "nvrtcCreateProgram failed");
+  char dtd[64], dtda[64];
+  snprintf(dtd, sizeof dtd, "-DPCPD_JIT_TD=0x%08xu", td);
+  snprintf(dtda, sizeof dtda, "-DPCPD_JIT_TDA=0x%08xu", tda);
+  const char *opts[] = {"-arch=sm_103a", "-std=c++17", "-default-device", dtd, dtda};
+  const nvrtcResult rc = J.compile(prog, 5, opts);
+  if (rc != NVRTC_SUCCESS) {
+    size_t n = 0;
+    J.log_size(prog, &n);
+    std::string log(n, ' ');
+    J.log(prog, &log[0]);
+    J.destroy(&prog);
+    return fail(PCPD_ECUDA, "runtime compile failed (%d): %.300s", (int)rc, log.c_str());
+  }
+  size_t cb = 0;
+  J.cubin_size(prog, &cb);
+  std::vector<char> cubin(cb);
+  J.cubin(prog, cubin.data());
+  J.destroy(&prog);
+  CUmodule mod = nullptr;
+  CUfunction fn = nullptr;
+  if (J.load(&mod, cubin.data()) != CUDA_SUCCESS || J.get_fn(&fn, mod, "pcpd_jit_sweep") != CUDA_SUCCESS)
+    return fail(PCPD_ECUDA, "loading the runtime-compiled sweep failed");
+  int optin = 0, stat = 0;
+  int rc2 = smem_optin(&optin);
+  if (rc2) return rc2;
+  J.get_attr(&stat, CU_FUNC_ATTRIBUTE_SHARED_SIZE_BYTES, fn);
+  if (J.set_attr(fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, optin - stat) != CUDA_SUCCESS)
+    return fail(PCPD_ECUDA, "setting the shared-memory limit of the runtime-compiled sweep failed");
+  g_jit[key] = fn;   // modules stay loaded until the process exits
+  *out = fn;
   return PCPD_OK;
 }
 
@@ -383,8 +508,15 @@ int launch_sweep(pcpd_t *h, uint64_t n_end, const std::vector<uint64_t> &subs, s
     B.tile_words = (uint32_t)h->tile_words;
     B.spin_limit = kSpinLimit;
     const int grid = (int)((uint64_t)h->grid < B.n_items ? (uint64_t)h->grid : B.n_items);
-    pcpdk::k_sweep_persistent<false><<<grid, h->threads, h->dyn_smem, h->stream>>>(B);
-    CU(cudaGetLastError());
+    if (h->jit_fn) {
+      void *args[] = {&B};
+      const CUresult r = g_jit_api.launch(h->jit_fn, grid, 1, 1, h->threads, 1, 1, (unsigned)h->dyn_smem,
+                                          (CUstream)h->stream, args, nullptr);
+      if (r != CUDA_SUCCESS) return fail(PCPD_ECUDA, "launch of the runtime-compiled sweep failed (%d)", (int)r);
+    } else {
+      pcpdk::k_sweep_persistent<false><<<grid, h->threads, h->dyn_smem, h->stream>>>(B);
+      CU(cudaGetLastError());
+    }
     g_launches.fetch_add(1, std::memory_order_relaxed);
     if (epochs & 1u) h->cur = 1 - h->cur;
     h->n_now = nb;
@@ -478,6 +610,25 @@ int pcpd_create_ex(const pcpd_params *prm, pcpd_t **out) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return bail(fail(PCPD_ECUDA, "init launch: %s", cudaGetErrorString(e)));
   g_launches.fetch_add(1, std::memory_order_relaxed);
+  // specialised sweep: thresholds strictly inside (0, 2^32) only
+  const bool normal = !h->T.td_full && !h->T.tda_full && h->T.td != 0u && h->T.tda != 0u;
+  const bool want = prm->jit > 0 || (prm->jit == 0 && (uint64_t)h->G * h->L >= (1ull << 22));
+  if (normal && want) {
+    CUfunction fn = nullptr;
+    if (jit_function(h->T.td, h->T.tda, &fn) == PCPD_OK) {
+      int per_sm = 0, sms = 0, dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (g_jit_api.occupancy(&per_sm, fn, (int)h->threads, h->dyn_smem) == CUDA_SUCCESS &&
+          per_sm >= 1) {
+        h->jit_fn = fn;
+        h->grid = per_sm * sms;
+      }
+    } else if (prm->jit > 0) {
+      return bail(PCPD_ECUDA);   // asked for explicitly: report why
+    }
+    g_err.clear();
+  }
   *out = h;
   return PCPD_OK;
 }
@@ -577,6 +728,7 @@ int pcpd_get_plan(const pcpd_t *h, pcpd_plan_info *out) {
   out->n_seg = h->n_seg;
   out->tiles = h->tiles;
   out->grid = (uint32_t)h->grid;
+  out->jit = h->jit_fn ? 1u : 0u;
   out->smem_bytes = h->dyn_smem;
   return PCPD_OK;
 }

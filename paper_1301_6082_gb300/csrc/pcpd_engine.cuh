@@ -12,7 +12,24 @@
 // Counter-based random numbers (keyed by instance seed, group, sub-step, window) make every
 // schedule, batching and tiling give the same bits as a lone run.
 #pragma once
+#ifndef PCPD_JIT_SOURCE
 #include "pcpd_kernels.cuh"
+#endif
+
+// Threshold compare of the sweep: generic (thresholds read as kernel constants) or, in a
+// build specialised for one (T_D, T_DA) pair (PCPD_JIT_TD / PCPD_JIT_TDA defined, both in
+// (0, 2^32)), with the thresholds as compile-time constants.  Same arithmetic, same bits.
+#ifdef PCPD_JIT_TD
+#define PCPD_CMP_D(c, w, K, m_hi) cmp_group_ct<(uint32_t)(PCPD_JIT_TD), K>(c, w, m_hi)
+#define PCPD_CMP_A(c, w, K, m_hi) cmp_group_ct<(uint32_t)(PCPD_JIT_TDA), K>(c, w, m_hi)
+#define PCPD_LO_D (__ffs((int)(PCPD_JIT_TD)) - 1u)
+#define PCPD_LO_DA (__ffs((int)(PCPD_JIT_TDA)) - 1u)
+#else
+#define PCPD_CMP_D(c, w, K, m_hi) cmp_group<K>(c, w, D.T.tmD, m_hi)
+#define PCPD_CMP_A(c, w, K, m_hi) cmp_group<K>(c, w, D.T.tmA, m_hi)
+#define PCPD_LO_D (D.T.lo_d)
+#define PCPD_LO_DA (D.T.lo_da)
+#endif
 
 namespace pcpdk {
 
@@ -196,10 +213,10 @@ __device__ __forceinline__ void run_item(const InstDesc &D, uint32_t *smem, uint
         philox4x32_10_rk(z0, z1, z2, z3, D.rk);
         O = x0;
         const uint32_t w[11] = {x1, x2, x3, y0, y1, y2, y3, z0, z1, z2, z3};   // planes 31..21
-        cmp_group<11>(cD, w, D.T.tmD, 31);
-        cmp_group<11>(cA, w, D.T.tmA, 31);
+        PCPD_CMP_D(cD, w, 11, 31);
+        PCPD_CMP_A(cA, w, 11, 31);
       }
-      const bool open = cmp_open2(cD, D.T.lo_d, 21) || cmp_open2(cA, D.T.lo_da, 21);
+      const bool open = cmp_open2(cD, PCPD_LO_D, 21) || cmp_open2(cA, PCPD_LO_DA, 21);
       if (valid && !open) apply_window(sm, ia, ib, ic, O, cD.lt, cA.lt);
       if (valid && open) {
         const uint32_t p3 = atomicAdd(s_q3n, 1u);
@@ -271,7 +288,7 @@ __device__ __forceinline__ const InstDesc &descriptor<true>(const BatchParams &,
 }
 
 template <bool BATCH>
-__global__ void __launch_bounds__(1024, 1) k_sweep_persistent(const BatchParams B) {
+__device__ __forceinline__ void sweep_body(const BatchParams &B) {
   extern __shared__ __align__(128) uint32_t smem[];
   __shared__ uint32_t s_phi[kPhiChunk];
   __shared__ unsigned int s_red[33];
@@ -416,6 +433,11 @@ __global__ void __launch_bounds__(1024, 1) k_sweep_persistent(const BatchParams 
   }
   // parity is per-thread-0 state; nothing else to release (no TMEM, no outstanding copies
   // except after a timed-out wait, which ends the CTA after the error is recorded)
+}
+
+template <bool BATCH>
+__global__ void __launch_bounds__(1024, 1) k_sweep_persistent(const BatchParams B) {
+  sweep_body<BATCH>(B);
 }
 
 }  // namespace pcpdk

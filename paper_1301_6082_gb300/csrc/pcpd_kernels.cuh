@@ -10,7 +10,9 @@
 // the dyadic AND/OR masks of Sec. 4.2-4.3.  Random words come from Philox4x32-10 (Salmon et
 // al., SC'11) keyed by the seed and counted by (window, sub-step, group, tag|block).
 #pragma once
+#ifndef __CUDACC_RTC__
 #include <cstdint>
+#endif
 
 namespace pcpdk {
 
@@ -108,6 +110,23 @@ __device__ __forceinline__ void cmp_group(Cmp &c, const uint32_t (&w)[K], const 
   for (int q = K - 1; q >= 0; --q) {
     const uint32_t t = tm[m_hi - q], P = w[q];
     b = (~P & t) | (~(P ^ t) & b);
+  }
+  c.lt |= c.eq & b;
+  c.eq = eq;
+}
+
+// The same fold with the threshold T a compile-time constant (a specialised build of the
+// engine for one (T_D, T_DA) pair): each plane's bit selects its operation, so two planes
+// merge into one logic operation where the compiler can.
+template <uint32_t T, int K>
+__device__ __forceinline__ void cmp_group_ct(Cmp &c, const uint32_t (&w)[K], int m_hi) {
+  uint32_t eq = c.eq, b = 0u;
+#pragma unroll
+  for (int q = 0; q < K; ++q) eq &= ((T >> (m_hi - q)) & 1u) ? w[q] : ~w[q];
+#pragma unroll
+  for (int q = K - 1; q >= 0; --q) {
+    const uint32_t P = w[q];
+    b = ((T >> (m_hi - q)) & 1u) ? (~P | b) : (~P & b);
   }
   c.lt |= c.eq & b;
   c.eq = eq;

@@ -33,13 +33,13 @@ class Params(C.Structure):
                 ("seed", C.c_uint64), ("init", C.c_int), ("stream", C.c_void_p),
                 ("dev_lattice", C.c_void_p), ("dev_bytes", C.c_size_t), ("per_sample", C.c_int),
                 ("plan_threads", C.c_uint32), ("plan_seg_sites", C.c_uint32), ("plan_tau", C.c_uint32),
-                ("autotune", C.c_int)]
+                ("autotune", C.c_int), ("jit", C.c_int)]
 
 
 class PlanInfo(C.Structure):
     _fields_ = [("ring", C.c_uint32), ("gpi", C.c_uint32), ("threads", C.c_uint32), ("core", C.c_uint32),
                 ("halo", C.c_uint32), ("tau", C.c_uint32), ("n_seg", C.c_uint32), ("tiles", C.c_uint32),
-                ("grid", C.c_uint32), ("pad_", C.c_uint32), ("smem_bytes", C.c_size_t)]
+                ("grid", C.c_uint32), ("jit", C.c_uint32), ("smem_bytes", C.c_size_t)]
 
 
 class ServerConfig(C.Structure):
@@ -144,13 +144,14 @@ class Pcpd:
     def __init__(self, L: int, samples: int, p: float, d: float, seed: int = 1,
                  init: int = INIT_FULL, per_sample: bool = False, stream=None,
                  dev_lattice=None, plan_threads: int = 0, plan_seg_sites: int = 0,
-                 plan_tau: int = 0, autotune: bool = False):
+                 plan_tau: int = 0, autotune: bool = False, jit: int = 0):
         lib = load()
         prm = Params()
         prm.L, prm.samples, prm.p, prm.d, prm.seed, prm.init = L, samples, p, d, seed, init
         prm.per_sample = 1 if per_sample else 0
         prm.plan_threads, prm.plan_seg_sites, prm.plan_tau = plan_threads, plan_seg_sites, plan_tau
         prm.autotune = 1 if autotune else 0
+        prm.jit = jit
         if stream is not None:
             prm.stream = C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
         self._keep = dev_lattice
@@ -241,7 +242,7 @@ class Pcpd:
     def plan(self) -> dict:
         info = PlanInfo()
         _check(load().pcpd_get_plan(self._h, C.byref(info)))
-        return {f: getattr(info, f) for f, _ in PlanInfo._fields_ if f != "pad_"}
+        return {f: getattr(info, f) for f, _ in PlanInfo._fields_}
 
 
 class Batch:

@@ -212,3 +212,23 @@ def test_live_handles_with_different_tiles(P):
         np.testing.assert_array_equal(s.lattice(), a.lattice())
         a.close()
         s.close()
+
+
+@pytest.mark.parametrize("L,seg,d,p", [(3000, 1000, 0.5, 0.15), (3000, 1000, 0.1, 0.11), (1000, 0, 0.9, 0.18),
+                                       (20000, 6000, 0.3, 0.7), (777, 0, 0.25, 0.05)])
+def test_runtime_specialised_sweep_bit_exact(P, oracle_mod, L, seg, d, p):
+    # the sweep compiled at run time for this (T_D, T_DA) pair == the generic sweep == oracle
+    S, seed = 64, 31
+    ts = [2, 9, 25]
+    a = P.Pcpd(L, S, p, d, seed=seed, init=INIT_HALF, plan_seg_sites=seg, plan_tau=32 if seg else 0, jit=1)
+    assert a.plan()["jit"] == 1
+    a.run(ts[-1], ts)
+    b = P.Pcpd(L, S, p, d, seed=seed, init=INIT_HALF, plan_seg_sites=seg, plan_tau=32 if seg else 0, jit=-1)
+    assert b.plan()["jit"] == 0
+    b.run(ts[-1], ts)
+    np.testing.assert_array_equal(a.lattice(), b.lattice())
+    np.testing.assert_array_equal(a.counts(), b.counts())
+    subs = [oracle_mod.substep_of_time(L, t) for t in ts]
+    st, tot, _ = _oracle_run(oracle_mod, L, S, p, d, seed, INIT_HALF, subs[-1], subs)
+    np.testing.assert_array_equal(a.counts(), tot)
+    np.testing.assert_array_equal(a.lattice(), oracle_mod.pack(st))
