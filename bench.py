@@ -32,6 +32,9 @@ from paper_1301_6082_gb300.replicas import combine, replica_seed  # noqa: E402
 from paper_1301_6082_gb300.workloads import SMEM_L65536, batch_instances, log_times, request_stream  # noqa: E402
 
 METRIC = "attempted site updates/s"
+# dram__bytes_read.sum + dram__bytes_write.sum of one bench-size launch of the specialised
+# sweep (one run advanced 2000 MCS), 1-pass ncu capture (profiles/pcpd_jit_sweep_L65536_S4096.md)
+TRAFFIC_PER_LAUNCH = 39.70e6 + 821.50e6
 UNIT = "attempts/s"
 
 
@@ -148,7 +151,9 @@ def batch_leg(pcpd, mcs_div: int = 100):
     attempts = sum(m["S"] * (m["L"] // 3) * pcpd.substep_of_time(m["L"], m["mcs_run"]) for m in mix)
     stream = torch.cuda.Stream()
     # plain
-    sims = [pcpd.Pcpd(m["L"], m["S"], m["p"], m["d"], seed=m["seed"], init=m["init"], stream=stream) for m in mix]
+    # both sides run the generic engine (a batch shares one kernel across thresholds)
+    sims = [pcpd.Pcpd(m["L"], m["S"], m["p"], m["d"], seed=m["seed"], init=m["init"], stream=stream, jit=-1)
+            for m in mix]
     torch.cuda.synchronize()
     l0 = pcpd.kernel_launches()
     t0 = time.perf_counter()
@@ -207,11 +212,12 @@ def stream_leg(pcpd, substeps: int = 2048):
             "hbm_gbs_algorithmic": hbm, "hbm_frac_of_measured_copy": hbm / 6787.2}
 
 
-def serving_leg(pcpd, seconds: float = 8.0, mcs_scale: float = 1 / 400, rate_hz: float = 200.0):
+def serving_leg(pcpd, seconds: float = 8.0, mcs_scale: float = 1 / 600, rate_hz: float = 200.0):
     """Poisson request stream (200 req/s; L log-uniform 2^10..2^20, 64..4096 samples,
     p in [.05,.25], d in [.1,.9], MCS log-uniform 1e3..1e5) for `seconds` instead of 60 s and
     with every MCS count scaled by mcs_scale (declared: the stream as specified offers
-    ~7.6e14 attempts/s, hundreds of times one GPU's capacity).  Reports throughput and
+    ~7.6e14 attempts/s, hundreds of times one GPU's capacity; x 1/600 offers ~1.5e12/s, about
+    three quarters of the batched engine's capacity).  Reports throughput and
     p50/p99 latency from submission to result."""
     import numpy as np
     reqs = request_stream(rate_hz, seconds, seed=1, mcs_scale=mcs_scale)
@@ -357,14 +363,20 @@ def main():
     sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak = sm_count * 4 * 32 * sm_max_mhz * 1e6 / 1e12   # T lane-ops/s
     achieved = (alg_ops / (ms / 1e3)) / 1e12
+    plan0 = sims[0].plan()
+    kname = "pcpd_jit_sweep (engine compiled for the run's thresholds)" if plan0.get("jit") else "k_sweep_persistent"
+    # Pipe-aware ceiling of the same work (measured on this GPU): Philox's 32x32->64 multiplies
+    # run at 1/4 of the issue rate on the FMA pipe (5.05e11 Philox blocks/s), so at the
+    # method's expected blocks per item the attempt rate cannot exceed 5.05e11*32/blocks.
+    philox_cap = sum(5.05e11 * 32.0 / o[1] for o in ops_item) / len(ops_item)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                 "frac": achieved / peak,
-                # dram__bytes_read.sum + dram__bytes_write.sum of one bench-size launch (one run,
-                # 2000 MCS = 6001 sub-steps), 1-pass ncu capture; profiles/k_sweep_persistent_L65536_S4096.md
-                "traffic": 38.21e6 + 803.47e6,
-                "kernel": "k_sweep_persistent (segmented tiles 32768+2x256 sites, tau=128)",
+                "traffic": TRAFFIC_PER_LAUNCH if plan0.get("jit") else None,
+                "kernel": f"{kname}; tiles {plan0['core']}+2x{plan0['halo']} sites, tau={plan0['tau']}",
                 "peak_note": f"{sm_count} SMs x 4 SMSPs x 32 lanes x {sm_max_mhz:.0f} MHz issue slots (derived)",
-                "ops_per_attempt": [round(o[0] / 32, 3) for o in ops_item]}
+                "ops_per_attempt": [round(o[0] / 32, 3) for o in ops_item],
+                "philox_pipe_cap_attempts_per_s": philox_cap,
+                "frac_of_philox_pipe_cap": value / world / philox_cap}
 
     # end to end through the public API with host buffers (pinned), host<->device in the region
     e2e = None

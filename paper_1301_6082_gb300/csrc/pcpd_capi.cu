@@ -1213,6 +1213,7 @@ int pcpd_batch_add(pcpd_batch_t *b, const pcpd_params *prm, uint64_t steps_mcs,
   p2.stream = b->stream;
   p2.dev_lattice = nullptr;
   p2.dev_bytes = 0;
+  p2.jit = -1;   // batched launches run the generic engine (one kernel for many thresholds)
   pcpd_t *h = nullptr;
   int rc = pcpd_create_ex(&p2, &h);
   if (rc) return rc;
@@ -1386,6 +1387,7 @@ void server_loop(pcpd_server_t *sv) {
       pcpd_params p2 = r->prm;
       p2.stream = sv->stream;
       p2.dev_lattice = nullptr;
+      p2.jit = -1;   // serving rounds run the generic engine
       int rc = pcpd_create_ex(&p2, &r->h);
       if (rc == PCPD_OK) rc = ensure_records(r->h, r->rec_times.size());
       if (rc == PCPD_OK && !r->rec_times.empty()) {
