@@ -232,3 +232,40 @@ def test_runtime_specialised_sweep_bit_exact(P, oracle_mod, L, seg, d, p):
     st, tot, _ = _oracle_run(oracle_mod, L, S, p, d, seed, INIT_HALF, subs[-1], subs)
     np.testing.assert_array_equal(a.counts(), tot)
     np.testing.assert_array_equal(a.lattice(), oracle_mod.pack(st))
+
+
+@pytest.mark.parametrize("jit", [-1, 1])
+def test_many_groups_multi_column_tiles(P, oracle_mod, jit):
+    # 2048 groups on a short ring: tiles hold 4 whole columns each (one phase group); sampled
+    # groups against the oracle, per-sample records against the oracle for those groups
+    L, S, p, d, seed = 100, 65536, 0.2, 0.4, 9
+    ts = [3, 10]
+    sim = P.Pcpd(L, S, p, d, seed=seed, init=INIT_HALF, per_sample=True, jit=jit)
+    assert sim.plan()["gpi"] == 4
+    sim.run(ts[-1], ts)
+    lat = sim.lattice()
+    ps = np.stack([sim.sample_counts(r) for r in range(len(ts))])
+    subs = [oracle_mod.substep_of_time(L, t) for t in ts]
+    for g in (0, 1, 2, 3, 4, 777, 2047):
+        st = oracle_mod.init_state(L, 32, INIT_HALF, seed, g)
+        _, pso, _ = oracle_mod.run(st, p, d, seed, 0, subs[-1], subs, per_sample=True, group0=g)
+        np.testing.assert_array_equal(lat[g], oracle_mod.pack(st)[0], err_msg=f"group {g}")
+        np.testing.assert_array_equal(ps[:, 32 * g:32 * g + 32], pso, err_msg=f"group {g}")
+    tot = sim.counts()
+    np.testing.assert_array_equal(tot, ps.sum(1))
+
+
+def test_record_now_after_resume(P, oracle_mod):
+    L, S, p, d, seed = 500, 64, 0.15, 0.5, 21
+    a = P.Pcpd(L, S, p, d, seed=seed, init=INIT_HALF)
+    a.run(7)
+    saved, n = a.lattice(), a.substep
+    b = P.Pcpd(L, S, p, d, seed=seed, init=INIT_EMPTY)
+    b.set_lattice(saved, n)
+    b.run(5, [7, 9, 12])        # 7 = the current time: records the restored state
+    c = b.counts()
+    st = oracle_mod.init_state(L, S, INIT_HALF, seed)
+    subs = [oracle_mod.substep_of_time(L, t) for t in (7, 9, 12)]
+    tot, _, _ = oracle_mod.run(st, p, d, seed, 0, subs[-1], subs)
+    np.testing.assert_array_equal(c, tot)
+    assert b.num_records == 3 and list(b.record_times()) == [7, 9, 12]
