@@ -102,6 +102,11 @@ size_t pcpd_num_records(const pcpd_t *h);
 int pcpd_density(const pcpd_t *h, double *rho_out, uint64_t *counts_out, size_t n_times);
 int pcpd_record_times(const pcpd_t *h, uint64_t *times_out, size_t n_times);
 
+/* Occupied nearest-neighbour pairs (i, i+1 mod L), summed over samples, of the first n_times
+ * records: the pair density rho_pair = pairs / (L * samples), which the paper analyses beside
+ * the particle density (Sec. 5.3).  Waits. */
+int pcpd_pair_counts(const pcpd_t *h, uint64_t *counts_out, size_t n_times);
+
 /* Per-sample counts of record r into out[samples] (uint32, sample order 0..samples-1).
  * Needs per_sample at creation; else PCPD_ESTATE. */
 int pcpd_sample_counts(const pcpd_t *h, size_t r, uint32_t *out);
@@ -216,6 +221,9 @@ size_t pcpd_batch_size(const pcpd_batch_t *b);
 
 /* Record counts of instance i (occupied (site, sample) pairs, n <= its n_times). */
 int pcpd_batch_counts(const pcpd_batch_t *b, size_t i, uint64_t *counts_out, size_t n);
+
+/* Pair counts (see pcpd_pair_counts) of instance i. */
+int pcpd_batch_pair_counts(const pcpd_batch_t *b, size_t i, uint64_t *counts_out, size_t n);
 
 /* Final lattice of instance i, canonical layout (G*L words).  Waits. */
 int pcpd_batch_lattice(const pcpd_batch_t *b, size_t i, uint32_t *host_out);

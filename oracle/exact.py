@@ -156,6 +156,31 @@ def rs_attempt_small(v, L, t_d, t_p, site_w=None):
     return out
 
 
+def pair_occupation(L: int) -> np.ndarray:
+    """Occupied nearest-neighbour pairs (i, i+1 mod L) of every configuration."""
+    x = np.arange(1 << L)
+    rot = ((x >> 1) | ((x & 1) << (L - 1)))
+    both = x & rot
+    return np.array([bin(int(i)).count("1") for i in both], dtype=np.float64)
+
+
+def sched_observable(L: int, t_d: int, t_da: int, rec_sub, obs: np.ndarray, mode: str = "full"):
+    """Exact mean and variance of a per-configuration observable (divided by L) after each
+    sub-step count in rec_sub."""
+    v = start_vector(L, mode)
+    w = index_weights(L)
+    mean, var, n = [], [], 0
+    for r in rec_sub:
+        while n < r:
+            v = sched_substep(v, L, t_d, t_da, w)
+            n += 1
+        m1 = float(v @ obs) / L
+        m2 = float(v @ (obs * obs)) / (L * L)
+        mean.append(m1)
+        var.append(max(0.0, m2 - m1 * m1))
+    return np.array(mean), np.array(var)
+
+
 def occupation(L: int) -> np.ndarray:
     x = np.arange(1 << L)
     return np.array([bin(int(i)).count("1") for i in x], dtype=np.float64)

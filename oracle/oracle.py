@@ -54,7 +54,7 @@ def lib():
             L.orc_init.argtypes = [u8p, C.c_uint32, C.c_uint32, C.c_int, C.c_uint64, C.c_uint32]
             L.orc_init.restype = C.c_int
             L.orc_run.argtypes = [C.c_uint32, C.c_uint32, C.c_uint64, C.c_uint64, C.c_uint64, u8p,
-                                  C.c_uint64, C.c_uint64, u64p, C.c_uint32, u64p, u32p, u64p, C.c_int, C.c_uint32]
+                                  C.c_uint64, C.c_uint64, u64p, C.c_uint32, u64p, u32p, u64p, C.c_int, C.c_uint32, u64p]
             L.orc_run.restype = C.c_int
             L.orc_rs_run.argtypes = [C.c_uint32, C.c_uint32, C.c_uint64, C.c_uint64, C.c_uint64, u8p,
                                      C.c_uint64, C.c_uint64, u64p, C.c_uint32, u64p, u32p, C.c_int]
@@ -119,10 +119,12 @@ def unpack(words: np.ndarray) -> np.ndarray:
 
 
 def run(state: np.ndarray, p: float, d: float, seed: int, n_begin: int, n_end: int,
-        rec_sub=(), per_sample: bool = False, threads: int | None = None, group0: int = 0):
+        rec_sub=(), per_sample: bool = False, threads: int | None = None, group0: int = 0,
+        pairs: bool = False):
     """Advance ``state`` (modified in place, [S][L] bytes: groups group0, group0+1, ... of an
     instance) from sub-step n_begin to n_end on the window schedule.
-    Returns (totals u64[R], per-sample u32[R][S] or None, events[3])."""
+    Returns (totals u64[R], per-sample u32[R][S] or None, events[3]), plus the occupied
+    nearest-neighbour pair counts u64[R] as a fourth element when ``pairs``."""
     assert state.dtype == np.uint8 and state.flags.c_contiguous
     S, L = state.shape
     td, tda, _ = thresholds(p, d)
@@ -130,14 +132,18 @@ def run(state: np.ndarray, p: float, d: float, seed: int, n_begin: int, n_end: i
     tot = np.zeros(len(rec), dtype=np.uint64)
     ps = np.zeros((len(rec), S), dtype=np.uint32) if per_sample else None
     ev = np.zeros(3, dtype=np.uint64)
+    prs = np.zeros(len(rec), dtype=np.uint64)
     nt = threads if threads is not None else (os.cpu_count() or 1)
     rc = lib().orc_run(L, S, td, tda, C.c_uint64(seed), _p(state, C.c_uint8), n_begin, n_end,
                        _p(rec, C.c_uint64), len(rec), _p(tot, C.c_uint64),
-                       _p(ps, C.c_uint32) if ps is not None else None, _p(ev, C.c_uint64), nt, group0)
+                       _p(ps, C.c_uint32) if ps is not None else None, _p(ev, C.c_uint64), nt, group0,
+                       _p(prs, C.c_uint64))
     if rc == 2:
         raise AssertionError("oracle: a window changed the particle number by other than +1, -2, 0")
     if rc != 0:
         raise ValueError("oracle: bad arguments")
+    if pairs:
+        return tot, ps, ev, prs
     return tot, ps, ev
 
 

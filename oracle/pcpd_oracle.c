@@ -182,6 +182,7 @@ typedef struct {
     const uint64_t *rec_sub;
     uint32_t n_rec;
     uint64_t *rec_total;   /* [n_rec], summed over all threads under a mutex */
+    uint64_t *rec_pairs;   /* [n_rec] occupied nearest-neighbour pairs, or NULL */
     uint32_t *rec_sample;  /* [n_rec][S] or NULL */
     uint64_t *events;      /* [3]: diffusion swaps that moved a particle, annihilations, fissions */
     pthread_mutex_t *mu;
@@ -190,13 +191,20 @@ typedef struct {
     int bad;               /* set if a window changed N by something other than +1,-2,0 */
 } orc_job;
 
-static void orc_count(orc_job *jb, uint32_t g, uint32_t r, uint64_t *tot)
+/* Record r: occupied sites, and occupied nearest-neighbour pairs (i, i+1 mod L) -- the pair
+ * density the paper analyses beside the particle density (Sec. 5.3). */
+static void orc_count(orc_job *jb, uint32_t g, uint32_t r, uint64_t *tot, uint64_t *pairs)
 {
     for (uint32_t j = 0; j < 32; ++j) {
         uint32_t s = 32u * g + j;
-        uint32_t cnt = 0;
-        for (uint32_t i = 0; i < jb->L; ++i) cnt += jb->state[(uint64_t)s * jb->L + i];
+        const uint8_t *row = jb->state + (uint64_t)s * jb->L;
+        uint32_t cnt = 0, pc = 0;
+        for (uint32_t i = 0; i < jb->L; ++i) {
+            cnt += row[i];
+            pc += row[i] & row[(i + 1u) % jb->L];
+        }
         tot[r] += cnt;
+        pairs[r] += pc;
         if (jb->rec_sample) jb->rec_sample[(uint64_t)r * jb->S + s] = cnt;
     }
 }
@@ -206,6 +214,7 @@ static void *orc_worker(void *arg)
     orc_job *jb = (orc_job *)arg;
     const uint32_t L = jb->L, K = L / 3u;
     uint64_t *tot = (uint64_t *)calloc(jb->n_rec ? jb->n_rec : 1, sizeof(uint64_t));
+    uint64_t *prs = (uint64_t *)calloc(jb->n_rec ? jb->n_rec : 1, sizeof(uint64_t));
     uint64_t ev[3] = {0, 0, 0};
     for (uint32_t g = jb->g_begin; g < jb->g_end; ++g) {
         const uint32_t gk = jb->g0 + g;        /* the group's index in the full instance */
@@ -214,7 +223,7 @@ static void *orc_worker(void *arg)
         while (r < jb->n_rec && jb->rec_sub[r] < jb->n_begin) ++r;
         for (uint64_t n = jb->n_begin;; ++n) {
             /* records of the state after n sub-steps */
-            while (r < jb->n_rec && jb->rec_sub[r] == n) { orc_count(jb, g, r, tot); ++r; }
+            while (r < jb->n_rec && jb->rec_sub[r] == n) { orc_count(jb, g, r, tot, prs); ++r; }
             if (n == jb->n_end) break;
             const uint32_t phi = orc_phase(jb->seed, L, h, (uint32_t)n);
             for (uint32_t k = 0; k < K; ++k) {
@@ -244,10 +253,14 @@ static void *orc_worker(void *arg)
         }
     }
     pthread_mutex_lock(jb->mu);
-    for (uint32_t r = 0; r < jb->n_rec; ++r) jb->rec_total[r] += tot[r];
+    for (uint32_t r = 0; r < jb->n_rec; ++r) {
+        jb->rec_total[r] += tot[r];
+        if (jb->rec_pairs) jb->rec_pairs[r] += prs[r];
+    }
     if (jb->events) for (int e = 0; e < 3; ++e) jb->events[e] += ev[e];
     pthread_mutex_unlock(jb->mu);
     free(tot);
+    free(prs);
     return NULL;
 }
 
@@ -255,20 +268,24 @@ static void *orc_worker(void *arg)
  * Run the window schedule from the state after n_begin sub-steps to the state after n_end.
  * The state holds the S/32 groups g0, g0+1, ... of an instance (g0 = 0 for all of it).
  * rec_sub: sorted sub-step indices in [n_begin, n_end]; the state after rec_sub[r] sub-steps
- * is counted into rec_total[r] (+= over all samples) and rec_sample[r][s] (if non-NULL).
+ * is counted into rec_total[r] (+= over all samples), rec_sample[r][s] (if non-NULL) and the
+ * occupied nearest-neighbour pairs into rec_pairs[r] (if non-NULL).
  * events (nullable, [3]) accumulates moving swaps, annihilations and fissions.
  * Returns 0, or 1 on bad arguments, or 2 if the particle-number invariant failed.
  */
 int orc_run(uint32_t L, uint32_t S, uint64_t t_d, uint64_t t_da, uint64_t seed,
             uint8_t *state, uint64_t n_begin, uint64_t n_end, const uint64_t *rec_sub,
             uint32_t n_rec, uint64_t *rec_total, uint32_t *rec_sample, uint64_t *events,
-            int n_threads, uint32_t g0)
+            int n_threads, uint32_t g0, uint64_t *rec_pairs)
 {
     if (L < 3 || S % 32u || n_end < n_begin || n_end > 0xFFFFFFFFull) return 1;
     const uint32_t G = S / 32u;
     if (n_threads < 1) n_threads = 1;
     if ((uint32_t)n_threads > G) n_threads = (int)G;
-    for (uint32_t r = 0; r < n_rec; ++r) rec_total[r] = 0;
+    for (uint32_t r = 0; r < n_rec; ++r) {
+        rec_total[r] = 0;
+        if (rec_pairs) rec_pairs[r] = 0;
+    }
     if (events) events[0] = events[1] = events[2] = 0;
     pthread_mutex_t mu = PTHREAD_MUTEX_INITIALIZER;
     orc_job *jobs = (orc_job *)calloc((size_t)n_threads, sizeof(orc_job));
@@ -279,6 +296,7 @@ int orc_run(uint32_t L, uint32_t S, uint64_t t_d, uint64_t t_da, uint64_t seed,
         jb->state = state; jb->n_begin = n_begin; jb->n_end = n_end;
         jb->rec_sub = rec_sub; jb->n_rec = n_rec; jb->rec_total = rec_total;
         jb->rec_sample = rec_sample; jb->events = events; jb->mu = &mu;
+        jb->rec_pairs = rec_pairs;
         jb->g_begin = (uint32_t)((uint64_t)G * t / n_threads);
         jb->g_end = (uint32_t)((uint64_t)G * (t + 1) / n_threads);
         jb->g0 = g0;

@@ -147,6 +147,7 @@ struct pcpd {
   // records
   std::vector<uint64_t> rec_times;
   unsigned long long *d_rec_total = nullptr;
+  unsigned long long *d_rec_pairs = nullptr;
   uint32_t *d_rec_sample = nullptr;
   size_t rec_cap = 0;
   uint32_t *d_rec_sub = nullptr;
@@ -342,7 +343,7 @@ int make_plan(pcpd_t *h, const pcpd_params *prm) {
   } else {
     h->ring = false;
     h->gpi = 1;
-    h->halo = 2u * h->tau;
+    h->halo = 2u * h->tau + 4u;   // 2 sites per sub-step, + one valid site past the core (pair records)
     uint32_t core;
     if (seg_override) {
       core = seg_override;
@@ -381,10 +382,12 @@ int ensure_records(pcpd_t *h, size_t need) {
   if (need <= h->rec_cap) return PCPD_OK;
   size_t cap = h->rec_cap ? h->rec_cap : 64;
   while (cap < need) cap *= 2;
-  unsigned long long *nt = nullptr;
+  unsigned long long *nt = nullptr, *np = nullptr;
   uint32_t *ns = nullptr;
   CU(cudaMalloc(&nt, cap * sizeof(unsigned long long)));
+  CU(cudaMalloc(&np, cap * sizeof(unsigned long long)));
   CU(cudaMemsetAsync(nt, 0, cap * sizeof(unsigned long long), h->stream));
+  CU(cudaMemsetAsync(np, 0, cap * sizeof(unsigned long long), h->stream));
   if (h->per_sample) {
     CU(cudaMalloc(&ns, cap * (size_t)h->S * sizeof(uint32_t)));
     CU(cudaMemsetAsync(ns, 0, cap * (size_t)h->S * sizeof(uint32_t), h->stream));
@@ -392,13 +395,16 @@ int ensure_records(pcpd_t *h, size_t need) {
   const size_t have = h->rec_times.size();
   if (have) {
     CU(cudaMemcpyAsync(nt, h->d_rec_total, have * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, h->stream));
+    CU(cudaMemcpyAsync(np, h->d_rec_pairs, have * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, h->stream));
     if (h->per_sample)
       CU(cudaMemcpyAsync(ns, h->d_rec_sample, have * (size_t)h->S * sizeof(uint32_t), cudaMemcpyDeviceToDevice, h->stream));
   }
   CU(cudaStreamSynchronize(h->stream));
   cudaFree(h->d_rec_total);
+  cudaFree(h->d_rec_pairs);
   cudaFree(h->d_rec_sample);
   h->d_rec_total = nt;
+  h->d_rec_pairs = np;
   h->d_rec_sample = ns;
   h->rec_cap = cap;
   return PCPD_OK;
@@ -441,6 +447,7 @@ void fill_desc(const pcpd_t *h, pcpdk::InstDesc &D, uint64_t n_begin, uint64_t n
   D.rec_sub = h->d_rec_sub ? h->d_rec_sub + ri : nullptr;
   D.rec_total = h->d_rec_total ? h->d_rec_total + slot : nullptr;
   D.rec_sample = h->per_sample ? h->d_rec_sample + slot * (size_t)h->S : nullptr;
+  D.rec_pairs = h->d_rec_pairs ? h->d_rec_pairs + slot : nullptr;
   D.done = h->d_done;
   D.rk = pcpdk::make_round_keys(h->k0, h->k1);
   D.T = h->T;
@@ -496,6 +503,7 @@ int launch_sweep(pcpd_t *h, uint64_t n_end, const std::vector<uint64_t> &subs, s
     D.rec_sub = h->d_rec_sub + ri;
     D.rec_total = h->d_rec_total ? h->d_rec_total + slot0 + ri : nullptr;
     D.rec_sample = h->per_sample ? h->d_rec_sample + (slot0 + ri) * (size_t)h->S : nullptr;
+    D.rec_pairs = h->d_rec_pairs ? h->d_rec_pairs + slot0 + ri : nullptr;
     D.done = h->d_done;
     D.rk = pcpdk::make_round_keys(h->k0, h->k1);
     D.T = h->T;
@@ -651,6 +659,7 @@ void pcpd_destroy(pcpd_t *h) {
   if (h->own_mem) cudaFree(h->buf[0]);
   cudaFree(h->d_done);
   cudaFree(h->d_rec_total);
+  cudaFree(h->d_rec_pairs);
   cudaFree(h->d_rec_sample);
   cudaFree(h->d_rec_sub);
   if (h->own_stream) cudaStreamDestroy(h->stream);
@@ -684,7 +693,8 @@ int pcpd_run(pcpd_t *h, uint64_t steps_mcs, const uint64_t *times, size_t n_time
   size_t slot = slot0;
   if (now_first) {
     pcpdk::k_count<<<h->G, 256, 0, h->stream>>>(h->buf[h->cur], h->L, h->pitch, h->S, h->d_rec_total + slot,
-                                                 h->per_sample ? h->d_rec_sample + slot * (size_t)h->S : nullptr);
+                                                 h->per_sample ? h->d_rec_sample + slot * (size_t)h->S : nullptr,
+                                                 h->d_rec_pairs + slot);
     CU(cudaGetLastError());
     g_launches.fetch_add(1, std::memory_order_relaxed);
     ++slot;
@@ -766,6 +776,19 @@ int pcpd_record_times(const pcpd_t *h, uint64_t *times_out, size_t n) {
   return PCPD_OK;
 }
 
+int pcpd_pair_counts(const pcpd_t *h, uint64_t *counts_out, size_t n) {
+  if (!h || (n && !counts_out)) return fail(PCPD_EINVAL, "NULL argument");
+  if (n > h->rec_times.size()) return fail(PCPD_EINVAL, "only %zu records", h->rec_times.size());
+  if (n == 0) return PCPD_OK;
+  std::vector<unsigned long long> c(n);
+  CU(cudaMemcpyAsync(c.data(), h->d_rec_pairs, n * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  int rc = check_engine(h);
+  if (rc) return rc;
+  for (size_t i = 0; i < n; ++i) counts_out[i] = c[i];
+  return PCPD_OK;
+}
+
 int pcpd_sample_counts(const pcpd_t *h, size_t r, uint32_t *out) {
   if (!h || !out) return fail(PCPD_EINVAL, "NULL argument");
   if (!h->per_sample) return fail(PCPD_ESTATE, "per-sample counts were not requested at creation");
@@ -793,6 +816,7 @@ int pcpd_set_lattice(pcpd_t *h, const uint32_t *host_in, uint64_t substep) {
   h->t_now = time_of_substep(h->L, substep);
   h->rec_times.clear();
   if (h->d_rec_total) CU(cudaMemsetAsync(h->d_rec_total, 0, h->rec_cap * sizeof(unsigned long long), h->stream));
+  if (h->d_rec_pairs) CU(cudaMemsetAsync(h->d_rec_pairs, 0, h->rec_cap * sizeof(unsigned long long), h->stream));
   if (h->d_rec_sample) CU(cudaMemsetAsync(h->d_rec_sample, 0, h->rec_cap * (size_t)h->S * 4, h->stream));
   return PCPD_OK;
 }
@@ -1266,6 +1290,12 @@ int pcpd_batch_counts(const pcpd_batch_t *b, size_t i, uint64_t *counts_out, siz
   if (!b || i >= b->inst.size()) return fail(PCPD_EINVAL, "no instance %zu", i);
   if (!b->ran) return fail(PCPD_ESTATE, "batch has not run");
   return pcpd_density(b->inst[i], nullptr, counts_out, n);
+}
+
+int pcpd_batch_pair_counts(const pcpd_batch_t *b, size_t i, uint64_t *counts_out, size_t n) {
+  if (!b || i >= b->inst.size()) return fail(PCPD_EINVAL, "no instance %zu", i);
+  if (!b->ran) return fail(PCPD_ESTATE, "batch has not run");
+  return pcpd_pair_counts(b->inst[i], counts_out, n);
 }
 
 int pcpd_batch_lattice(const pcpd_batch_t *b, size_t i, uint32_t *host_out) {
@@ -1780,7 +1810,7 @@ extern "C" int pcpd_autotune(const pcpd_params *prm, uint32_t trial_substeps, pc
     for (uint32_t th : {512u, 1024u})
       for (uint32_t tau : {64u, 128u, 256u})
         for (uint32_t seg : {base.core, half}) {
-          if (seg + 4u * tau + 12u > prm->L || (prm->L + seg - 1) / seg < 2) continue;
+          if (seg + 2u * (2u * tau + 4u) + 12u > prm->L || (prm->L + seg - 1) / seg < 2) continue;
           cands.push_back({th, seg, tau});
         }
   }

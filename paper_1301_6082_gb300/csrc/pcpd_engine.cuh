@@ -3,8 +3,8 @@
 //
 // Item = (instance, epoch e, tile).  A tile is either a group of whole columns (RING: gpi
 // 32-sample groups that fit in shared memory, updated with periodic indexing) or one
-// segment of one column with a halo of H = 2*tau sites on each side (SEGMENT, temporal
-// blocking as in the tile kernel).  Epoch e covers sub-steps [n_begin + e*tau, ... + tau).
+// segment of one column with a halo of H >= 2*tau + 1 sites on each side (SEGMENT, temporal
+// blocking; the extra site keeps the one after the core valid for pair records).  Epoch e covers sub-steps [n_begin + e*tau, ... + tau).
 // Items are popped in list order from a device counter by persistent CTAs; an item of epoch
 // e > 0 first waits (bounded, acquire) until the tiles it reads -- itself and, for segments,
 // its two neighbours -- have completed epoch e-1.  Epoch e reads lattice buffer e&1 and
@@ -47,6 +47,7 @@ struct InstDesc {
   const uint32_t *rec_sub;   // [n_rec] sub-step of each record (increasing)
   unsigned long long *rec_total;  // [n_rec]
   uint32_t *rec_sample;      // [n_rec][S] or nullptr
+  unsigned long long *rec_pairs;  // [n_rec] occupied nearest-neighbour pairs, or nullptr
   uint32_t *done;            // [tiles per epoch] epochs completed in this launch
   RoundKeys rk;
   Thresholds T;
@@ -270,7 +271,8 @@ __device__ __forceinline__ void run_item(const InstDesc &D, uint32_t *smem, uint
     __syncthreads();
     if (r < D.n_rec && D.rec_sub[r] == n + 1u) {
       for (uint32_t c = 0; c < gpi; ++c)
-        tile_count(smem + c * L, H, H + core_len, D.rec_total, D.rec_sample, D.S, r, g0 + c, s_red);
+        tile_count(smem + c * L, H, H + core_len, D.rec_total, D.rec_sample, D.rec_pairs, D.S, r, g0 + c,
+                   RING ? L : 0u, s_red);
       ++r;
     }
   }
@@ -291,7 +293,7 @@ template <bool BATCH>
 __device__ __forceinline__ void sweep_body(const BatchParams &B) {
   extern __shared__ __align__(128) uint32_t smem[];
   __shared__ uint32_t s_phi[kPhiChunk];
-  __shared__ unsigned int s_red[33];
+  __shared__ unsigned int s_red[34];
   __shared__ unsigned int s_q3n;
   __shared__ unsigned long long s_item;
   __shared__ int s_abort;
@@ -300,7 +302,7 @@ __device__ __forceinline__ void sweep_body(const BatchParams &B) {
   uint32_t *q3 = smem + B.tile_words;
   uint32_t parity = 0;
   if (threadIdx.x == 0) mbar_init(&s_mbar);
-  for (uint32_t t = threadIdx.x; t <= 32u; t += blockDim.x) s_red[t] = 0;
+  for (uint32_t t = threadIdx.x; t <= 33u; t += blockDim.x) s_red[t] = 0;
   __syncthreads();
 
   for (;;) {

@@ -247,14 +247,29 @@ __device__ __forceinline__ uint32_t phase_of(uint32_t n, uint32_t h, uint32_t L,
 constexpr int kPhiChunk = 256;
 
 // Count occupied sites of tile words [y0, y1) of group g into record r: the total into
-// rec_total[r] and, if rec_sample is set, sample 32g+j's count into rec_sample[r*S + 32g + j].
+// rec_total[r], occupied nearest-neighbour pairs (y, y+1) into rec_pairs[r] -- the pair
+// density analysed beside the particle density in Sec. 5.3 -- and, if rec_sample is set,
+// sample 32g+j's count into rec_sample[r*S + 32g + j].  ring_len != 0: the words are a whole
+// ring of that length and the last site pairs with the first; otherwise word y1 (one past the
+// range) must be valid.  s_red: 34 zeroed shared words, left zeroed.
 __device__ __forceinline__ void tile_count(const uint32_t *sm, uint32_t y0, uint32_t y1,
                                            unsigned long long *rec_total, uint32_t *rec_sample,
-                                           uint32_t S, uint32_t r, uint32_t g, unsigned int *s_red) {
-  unsigned int local = 0;
-  for (uint32_t y = y0 + threadIdx.x; y < y1; y += blockDim.x) local += __popc(sm[y]);
+                                           unsigned long long *rec_pairs, uint32_t S, uint32_t r,
+                                           uint32_t g, uint32_t ring_len, unsigned int *s_red) {
+  unsigned int local = 0, pairs = 0;
+  for (uint32_t y = y0 + threadIdx.x; y < y1; y += blockDim.x) {
+    const uint32_t w = sm[y];
+    uint32_t yn = y + 1u;
+    if (ring_len && yn == ring_len) yn = 0u;
+    local += __popc(w);
+    pairs += __popc(w & sm[yn]);
+  }
   local = __reduce_add_sync(0xFFFFFFFFu, local);
-  if ((threadIdx.x & 31) == 0) atomicAdd(&s_red[32], local);
+  pairs = __reduce_add_sync(0xFFFFFFFFu, pairs);
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&s_red[32], local);
+    atomicAdd(&s_red[33], pairs);
+  }
   if (rec_sample) {
     unsigned int cnt[32];
 #pragma unroll
@@ -271,11 +286,14 @@ __device__ __forceinline__ void tile_count(const uint32_t *sm, uint32_t y0, uint
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0) atomicAdd(&rec_total[r], (unsigned long long)s_red[32]);
+  if (threadIdx.x == 0) {
+    atomicAdd(&rec_total[r], (unsigned long long)s_red[32]);
+    if (rec_pairs) atomicAdd(&rec_pairs[r], (unsigned long long)s_red[33]);
+  }
   if (rec_sample && threadIdx.x < 32)
     atomicAdd(&rec_sample[(size_t)r * S + 32u * g + threadIdx.x], s_red[threadIdx.x]);
   __syncthreads();
-  for (uint32_t t = threadIdx.x; t <= 32u; t += blockDim.x) s_red[t] = 0;
+  for (uint32_t t = threadIdx.x; t <= 33u; t += blockDim.x) s_red[t] = 0;
   __syncthreads();
 }
 
@@ -386,23 +404,29 @@ __global__ void k_init(uint32_t *lat, uint32_t L, uint32_t pitch, uint32_t G, in
 
 // Record of the current state (no sub-step): one CTA per group.
 __global__ void k_count(const uint32_t *lat, uint32_t L, uint32_t pitch, uint32_t S,
-                        unsigned long long *rec_total, uint32_t *rec_sample) {
+                        unsigned long long *rec_total, uint32_t *rec_sample,
+                        unsigned long long *rec_pairs) {
   const uint32_t g = blockIdx.x;
   const uint32_t *col = lat + (size_t)g * pitch;
-  unsigned int local = 0;
+  unsigned int local = 0, pairs = 0;
   unsigned int cnt[32];
 #pragma unroll
   for (int j = 0; j < 32; ++j) cnt[j] = 0;
   for (uint32_t i = threadIdx.x; i < L; i += blockDim.x) {
     const uint32_t w = col[i];
     local += __popc(w);
+    pairs += __popc(w & col[i + 1u == L ? 0u : i + 1u]);
     if (rec_sample) {
 #pragma unroll
       for (int j = 0; j < 32; ++j) cnt[j] += (w >> j) & 1u;
     }
   }
   local = __reduce_add_sync(0xFFFFFFFFu, local);
-  if ((threadIdx.x & 31) == 0) atomicAdd(rec_total, (unsigned long long)local);
+  pairs = __reduce_add_sync(0xFFFFFFFFu, pairs);
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(rec_total, (unsigned long long)local);
+    if (rec_pairs) atomicAdd(rec_pairs, (unsigned long long)pairs);
+  }
   if (rec_sample) {
 #pragma unroll
     for (int j = 0; j < 32; ++j) {

@@ -63,6 +63,7 @@ SIGNATURES = [
     ("pcpd_density", C.c_int, [C.c_void_p, _f64p, _u64p, C.c_size_t]),
     ("pcpd_record_times", C.c_int, [C.c_void_p, _u64p, C.c_size_t]),
     ("pcpd_sample_counts", C.c_int, [C.c_void_p, C.c_size_t, _u32p]),
+    ("pcpd_pair_counts", C.c_int, [C.c_void_p, _u64p, C.c_size_t]),
     ("pcpd_get_lattice", C.c_int, [C.c_void_p, _u32p]),
     ("pcpd_set_lattice", C.c_int, [C.c_void_p, _u32p, C.c_uint64]),
     ("pcpd_run_substeps", C.c_int, [C.c_void_p, C.c_uint64]),
@@ -84,6 +85,7 @@ SIGNATURES = [
     ("pcpd_batch_size", C.c_size_t, [C.c_void_p]),
     ("pcpd_batch_counts", C.c_int, [C.c_void_p, C.c_size_t, _u64p, C.c_size_t]),
     ("pcpd_batch_lattice", C.c_int, [C.c_void_p, C.c_size_t, _u32p]),
+    ("pcpd_batch_pair_counts", C.c_int, [C.c_void_p, C.c_size_t, _u64p, C.c_size_t]),
     ("pcpd_batch_destroy", None, [C.c_void_p]),
     ("pcpd_server_start", C.c_int, [C.POINTER(ServerConfig), C.POINTER(C.c_void_p)]),
     ("pcpd_server_submit", C.c_int, [C.c_void_p, C.POINTER(Params), C.c_uint64, _u64p, C.c_size_t, C.c_int,
@@ -207,6 +209,17 @@ class Pcpd:
             _check(load().pcpd_density(self._h, None, _ptr(c, C.c_uint64), n))
         return c
 
+    def pair_counts(self) -> np.ndarray:
+        """Occupied nearest-neighbour pairs per record, summed over samples."""
+        n = self.num_records
+        c = np.zeros(n, dtype=np.uint64)
+        if n:
+            _check(load().pcpd_pair_counts(self._h, _ptr(c, C.c_uint64), n))
+        return c
+
+    def pair_density(self) -> np.ndarray:
+        return self.pair_counts() / float(self.L * self.S)
+
     def density(self) -> np.ndarray:
         n = self.num_records
         r = np.zeros(n, dtype=np.float64)
@@ -276,6 +289,13 @@ class Batch:
         c = np.zeros(n, dtype=np.uint64)
         if n:
             _check(load().pcpd_batch_counts(self._h, i, _ptr(c, C.c_uint64), n))
+        return c
+
+    def pair_counts(self, i: int) -> np.ndarray:
+        n = self._meta[i][2]
+        c = np.zeros(n, dtype=np.uint64)
+        if n:
+            _check(load().pcpd_batch_pair_counts(self._h, i, _ptr(c, C.c_uint64), n))
         return c
 
     def lattice(self, i: int) -> np.ndarray:

@@ -43,14 +43,16 @@ def test_batch_equals_alone_and_oracle(P, oracle_mod):
         alone = P.Pcpd(L, S, p, d, seed=seed, init=init)
         alone.run(mcs, recs[i])
         np.testing.assert_array_equal(b.counts(i), alone.counts(), err_msg=f"instance {i}")
+        np.testing.assert_array_equal(b.pair_counts(i), alone.pair_counts(), err_msg=f"pairs, instance {i}")
         lat = b.lattice(i)
         np.testing.assert_array_equal(lat, alone.lattice(), err_msg=f"instance {i}")
         alone.close()
         if L * S * mcs <= 3_000_000:
             subs = [oracle_mod.substep_of_time(L, t) for t in recs[i]]
             st = oracle_mod.init_state(L, S, init, seed)
-            tot, _, _ = oracle_mod.run(st, p, d, seed, 0, subs[-1], subs)
+            tot, _, _, prs = oracle_mod.run(st, p, d, seed, 0, subs[-1], subs, pairs=True)
             np.testing.assert_array_equal(b.counts(i), tot, err_msg=f"oracle, instance {i}")
+            np.testing.assert_array_equal(b.pair_counts(i), prs, err_msg=f"oracle pairs, instance {i}")
             np.testing.assert_array_equal(lat, oracle_mod.pack(st), err_msg=f"oracle, instance {i}")
     b.close()
 

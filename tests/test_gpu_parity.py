@@ -94,9 +94,11 @@ def test_L1024_S64_full_run_bit_exact(P, oracle_mod):
     lat = sim.lattice()
     ps_gpu = np.stack([sim.sample_counts(r) for r in range(len(ts))])
     subs = [oracle_mod.substep_of_time(L, t) for t in ts]
-    st, tot, ps = _oracle_run(oracle_mod, L, S, p, d, seed, INIT_FULL, subs[-1], subs, per_sample=True)
+    st = oracle_mod.init_state(L, S, INIT_FULL, seed)
+    tot, ps, _, prs = oracle_mod.run(st, p, d, seed, 0, subs[-1], subs, per_sample=True, pairs=True)
     np.testing.assert_array_equal(got, tot)
     np.testing.assert_array_equal(ps_gpu, ps)
+    np.testing.assert_array_equal(sim.pair_counts(), prs)
     np.testing.assert_array_equal(lat, oracle_mod.pack(st))
     golden = np.loadtxt(__file__.replace("test_gpu_parity.py", "golden/pcpd_L1024_S64.txt"), dtype=np.uint64)
     np.testing.assert_array_equal(got, golden[:, 2])
@@ -134,8 +136,11 @@ def test_segmented_plan_bit_exact_and_plan_invariant(P, oracle_mod, L, seg, tau,
     np.testing.assert_array_equal(a.lattice(), b.lattice())
     np.testing.assert_array_equal(a.counts(), b.counts())
     subs = [oracle_mod.substep_of_time(L, t) for t in ts]
-    st, tot, _ = _oracle_run(oracle_mod, L, S, p, d, seed, INIT_HALF, subs[-1], subs)
+    st = oracle_mod.init_state(L, S, INIT_HALF, seed)
+    tot, _, _, prs = oracle_mod.run(st, p, d, seed, 0, subs[-1], subs, pairs=True)
     np.testing.assert_array_equal(a.counts(), tot)
+    np.testing.assert_array_equal(a.pair_counts(), prs)
+    np.testing.assert_array_equal(b.pair_counts(), prs)
     np.testing.assert_array_equal(a.lattice(), oracle_mod.pack(st))
 
 
@@ -229,8 +234,10 @@ def test_runtime_specialised_sweep_bit_exact(P, oracle_mod, L, seg, d, p):
     np.testing.assert_array_equal(a.lattice(), b.lattice())
     np.testing.assert_array_equal(a.counts(), b.counts())
     subs = [oracle_mod.substep_of_time(L, t) for t in ts]
-    st, tot, _ = _oracle_run(oracle_mod, L, S, p, d, seed, INIT_HALF, subs[-1], subs)
+    st = oracle_mod.init_state(L, S, INIT_HALF, seed)
+    tot, _, _, prs = oracle_mod.run(st, p, d, seed, 0, subs[-1], subs, pairs=True)
     np.testing.assert_array_equal(a.counts(), tot)
+    np.testing.assert_array_equal(a.pair_counts(), prs)
     np.testing.assert_array_equal(a.lattice(), oracle_mod.pack(st))
 
 

@@ -111,3 +111,35 @@ def test_rs_dimer_filling_jamming_limit(oracle_mod):
     # jammed: no adjacent pair is left anywhere
     assert not np.any(st & np.roll(st, -1, axis=1))
     assert abs(rho.mean() - math.exp(-2)) < 4 * rho.std(ddof=1) / math.sqrt(S) + 1.0 / L
+
+
+def test_pair_occupation_definition():
+    # bit i of x is site i; pairs (i, i+1 mod L)
+    occ = E.pair_occupation(4)
+    assert occ[0b1111] == 4 and occ[0] == 0 and occ[0b0011] == 1 and occ[0b1001] == 1 and occ[0b0101] == 0
+
+
+@pytest.mark.parametrize("L", [4, 7, 9])
+def test_pair_density_matches_exact_chain(oracle_mod, L):
+    # the pair density rho_pair = <q_i q_{i+1}> analysed beside rho in Sec. 5.3; batch means
+    # over 16 independent seeds (1024 samples each), 3 sigma
+    p, d = 0.15, 0.5
+    td, tda, _ = oracle_mod.thresholds(p, d)
+    rec = [0, 2, 5, 11, 24]
+    ex, var = E.sched_observable(L, td, tda, rec, E.pair_occupation(L), mode="half")
+    S, means = 1024, []
+    for seed in range(40, 56):
+        st = oracle_mod.init_state(L, S, INIT_HALF, seed)
+        _, _, _, prs = oracle_mod.run(st, p, d, seed, 0, rec[-1], rec, pairs=True)
+        means.append(prs.astype(float) / (L * S))
+    means = np.array(means)
+    m = means.mean(0)
+    se = np.maximum(means.std(0, ddof=1) / np.sqrt(len(means)), np.sqrt(var / (S * len(means))))
+    assert np.all(np.abs(m - ex) <= 3 * se + 1e-12), (m, ex, se)
+
+
+def test_pair_counts_closed_forms(oracle_mod):
+    for mode, want in ((0, 1.0), (1, 0.0)):
+        st = oracle_mod.init_state(30, 64, mode, 1)
+        tot, _, _, prs = oracle_mod.run(st, 0.0, 1.0, 1, 0, 5, [0, 5], pairs=True)
+        assert np.all(prs == want * 30 * 64)     # full ring: L pairs per sample; empty: none

@@ -26,6 +26,7 @@ MUTANTS = {
     "windows_cover_wrap": ("const uint32_t L = jb->L, K = L / 3u;", "const uint32_t L = jb->L, K = (L + 2u) / 3u;"),
     "diffusion_swaps_a_c": ("*sb = *q;\n        *q = tmp;", "*sb = *sb;\n        *sa = *sc; *sc = tmp; (void)q;"),
     "time_floor_not_ceil": ("return (uint64_t)((num + K - 1) / K);", "return (uint64_t)(num / K);"),
+    "pair_wrong_neighbour": ("pc += row[i] & row[(i + 1u) % jb->L];", "pc += row[i] & row[(i + 2u) % jb->L];"),
 }
 
 
@@ -60,6 +61,7 @@ def _pins(mod):
     yield "binomial_first_substep", lambda: TI.test_full_lattice_first_substep_binomial(mod, 0.15, 0.5)
     for L in (4, 5, 8, 9):
         yield f"exact_chain_L{L}", (lambda L=L: TE.test_schedule_oracle_matches_exact_chain(mod, L, 0.15, 0.5))
+    yield "pair_density_exact_L7", lambda: TE.test_pair_density_matches_exact_chain(mod, 7)
 
 
 def _caught(mod):
