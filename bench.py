@@ -137,6 +137,29 @@ def run_cpu_sample(budget_groups: int = 16, substeps: int = 300):
                       f"from full ({attempts:.3e} attempts, {dt:.1f} s)"}
 
 
+def run_rs_sample(samples: int = 256, mcs: int = 40):
+    """Alg. 1 (random-sequential, the paper's "conventional" dynamics) as the oracle runs it,
+    on L = 65536 with `samples` samples for `mcs` MCS from the full start: the analogue of the
+    paper's simple-CPU-program figure."""
+    from oracle import oracle as O
+    L = SMEM_L65536["L"]
+    cores = min(os.cpu_count() or 1, samples)
+    st = O.init_state(L, samples, O.MODE_FULL, 1)
+    t0 = time.perf_counter()
+    O.rs_run(st, 0.15, 0.5, 1, 0, mcs * L, threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": samples * L * mcs / dt, "unit": UNIT, "cores": cores,
+            "sample": f"Alg. 1 on L={L}, {samples} samples, {mcs} MCS ({dt:.1f} s)"}
+
+
+PAPER_CONTEXT = {
+    "note": "the paper's own numbers (Sec. 5.2), other hardware and schedule: context only",
+    "gpu_moves_per_s": 8.0e10, "gpu": "NVIDIA GTX 580 (Fermi), OpenCL via CUDA 4.0, d = 1/2, 32-bit multispin",
+    "gpu_over_simple_cpu": 4000, "gpu_over_same_algorithm_on_cpu": 130,
+    "cpu": "Intel Xeon E5620 2.4 GHz / Core 2 Duo E8400 3.0 GHz, gcc 4.1.2 -O2",
+}
+
+
 def batch_leg(pcpd, mcs_div: int = 100):
     """The 512-instance heterogeneous mix (L log-uniform 2^10..2^18, 64/256/1024 samples,
     d in {.1,...,.9}, p in [.05,.25], MCS log-uniform 1e3..1e5, full or half start, seeds
@@ -420,6 +443,7 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = run_cpu_sample()
+        cpu["alg1_random_sequential"] = run_rs_sample()
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -433,7 +457,8 @@ def main():
                            "l2": "inputs larger than L2: 3 lattices x 2 buffers x 32 MiB = 192 MiB, streamed per tile epoch",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-                "gpu_launches": launches, "batch": batch, "serving": serving, "streamed": streamed}
+                "gpu_launches": launches, "batch": batch, "serving": serving, "streamed": streamed,
+                "paper_context": dict(PAPER_CONTEXT, this_run_over_paper_gpu=value / PAPER_CONTEXT["gpu_moves_per_s"])}
         print(json.dumps(line), flush=True)
     for s in sims:
         s.close()

@@ -1,0 +1,39 @@
+"""The near-critical sweep driver: its batched densities equal separate lone runs summed."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1301_6082_gb300 import build, pcpd
+    build.build()
+    pcpd.load()
+    return pcpd
+
+
+def test_p_sweep_matches_lone_runs(P):
+    from paper_1301_6082_gb300.sweep import p_sweep
+    from paper_1301_6082_gb300.workloads import log_times
+    L, S, d, mcs = 2048, 64, 0.5, 60
+    ps, seeds = (0.12, 0.2), (3, 4)
+    out = p_sweep(d, ps, L, S, mcs, n_rec=10, seeds=seeds)
+    times = log_times(mcs, 10)
+    for p in ps:
+        tot = 0
+        prs = 0
+        for s in seeds:
+            a = P.Pcpd(L, S, p, d, seed=s)
+            a.run(mcs, times)
+            tot = tot + a.counts().astype(np.int64)
+            prs = prs + a.pair_counts().astype(np.int64)
+            a.close()
+        np.testing.assert_array_equal(out[p]["rho"], tot / (L * S * len(seeds)))
+        np.testing.assert_array_equal(out[p]["rho_pair"], prs / (L * S * len(seeds)))
+        assert np.all(out[p]["rho_pair"] <= out[p]["rho"])
+    # more annihilation, faster decay
+    assert out[0.2]["rho"][-1] < out[0.12]["rho"][-1]
