@@ -143,8 +143,9 @@ __device__ __forceinline__ void run_item(const InstDesc &D, uint32_t *smem, uint
   const uint32_t tile_len = core_len + 2u * H;
   const uint32_t base = RING ? 0u : (uint32_t)(((uint64_t)s0 + L - H) % L);
   const uint32_t h = (32u * g0) / 128u;   // one phase group for all gpi columns
-  const uint32_t n_a = D.n_begin + e * D.tau;
-  const uint32_t n_b = min(n_a + D.tau, D.n_end);
+  const uint32_t n_a = D.n_begin + e * D.tau;   // < n_end < 2^32
+  // the epoch's end in 64 bits: n_a + tau may pass 2^32 near the end of the counter range
+  const uint32_t n_b = (uint32_t)min((unsigned long long)n_a + D.tau, (unsigned long long)D.n_end);
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
 
   // first record after n_a

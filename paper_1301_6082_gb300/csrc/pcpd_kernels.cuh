@@ -138,27 +138,6 @@ __device__ __forceinline__ bool cmp_open2(const Cmp &c, uint32_t lo, int m_lo) {
   return c.eq != 0u && (uint32_t)m_lo > lo;
 }
 
-// Less/greater state of the MSB-first compare of 32 lanes against one threshold: lanes in
-// `lt` are decided u < T, lanes in `gt` decided u >= T, the rest match T's bits so far.
-__device__ __forceinline__ void cmp_plane(uint32_t &lt, uint32_t &gt, uint32_t plane, bool tbit) {
-  if (tbit) lt |= ~(gt | plane);   // T bit 1: an undecided lane with bit 0 is below T
-  else      gt |= plane & ~lt;     // T bit 0: an undecided lane with bit 1 is above T
-}
-
-// Plane m of threshold T.  Planes below T's lowest set bit change nothing that matters (a
-// lane that still equals T's prefix there is >= T either way), so they need no test.
-__device__ __forceinline__ void cmp_plane_if(uint32_t &lt, uint32_t &gt, uint32_t plane,
-                                             uint32_t t, uint32_t lo, int m) {
-  (void)lo;
-  cmp_plane(lt, gt, plane, (t >> m) & 1u);
-}
-
-// True while some lane is undecided against T after the planes down to m (inclusive) and T
-// still has a non-zero bit below m.
-__device__ __forceinline__ bool cmp_open(uint32_t lt, uint32_t gt, uint32_t lo, int m) {
-  return (uint32_t)m > lo && ((lt | gt) != 0xFFFFFFFFu);
-}
-
 // Rate masks of one (window k, sub-step n, group g): D = lanes with u < T_D (diffuse),
 // A = lanes with T_D <= u < T_DA (annihilate an occupied bond), O = orientation bits.
 // Block b of the counter (k, n, g, b) holds (O, P31, P30, P29) for b = 0 and
@@ -166,47 +145,6 @@ __device__ __forceinline__ bool cmp_open(uint32_t lt, uint32_t gt, uint32_t lo, 
 struct Masks {
   uint32_t D, A, O;
 };
-
-__device__ __forceinline__ Masks rate_masks(uint32_t k, uint32_t n, uint32_t g,
-                                            const RoundKeys &rk, const Thresholds &T) {
-  uint32_t ltD = T.td_full ? 0xFFFFFFFFu : 0u, gtD = (!T.td_full && T.td == 0u) ? 0xFFFFFFFFu : 0u;
-  uint32_t ltA = T.tda_full ? 0xFFFFFFFFu : 0u, gtA = (!T.tda_full && T.tda == 0u) ? 0xFFFFFFFFu : 0u;
-  uint32_t O;
-  {
-    uint32_t x0 = k, x1 = n, x2 = g, x3 = (kTagDyn << 28) | 0u;
-    philox4x32_10_rk(x0, x1, x2, x3, rk);
-    O = x0;
-    cmp_plane_if(ltD, gtD, x1, T.td, T.lo_d, 31);
-    cmp_plane_if(ltD, gtD, x2, T.td, T.lo_d, 30);
-    cmp_plane_if(ltD, gtD, x3, T.td, T.lo_d, 29);
-    cmp_plane_if(ltA, gtA, x1, T.tda, T.lo_da, 31);
-    cmp_plane_if(ltA, gtA, x2, T.tda, T.lo_da, 30);
-    cmp_plane_if(ltA, gtA, x3, T.tda, T.lo_da, 29);
-  }
-#pragma unroll
-  for (int b = 1; b <= 8; ++b) {
-    const int m_prev = 33 - 4 * b;  // lowest plane consumed so far
-    if (!cmp_open(ltD, gtD, T.lo_d, m_prev) && !cmp_open(ltA, gtA, T.lo_da, m_prev)) break;
-    uint32_t x0 = k, x1 = n, x2 = g, x3 = (kTagDyn << 28) | (uint32_t)b;
-    philox4x32_10_rk(x0, x1, x2, x3, rk);
-    const int m0 = 32 - 4 * b;  // plane of x0
-    cmp_plane_if(ltD, gtD, x0, T.td, T.lo_d, m0);
-    cmp_plane_if(ltA, gtA, x0, T.tda, T.lo_da, m0);
-    if (b < 8) {
-      cmp_plane_if(ltD, gtD, x1, T.td, T.lo_d, m0 - 1);
-      cmp_plane_if(ltD, gtD, x2, T.td, T.lo_d, m0 - 2);
-      cmp_plane_if(ltD, gtD, x3, T.td, T.lo_d, m0 - 3);
-      cmp_plane_if(ltA, gtA, x1, T.tda, T.lo_da, m0 - 1);
-      cmp_plane_if(ltA, gtA, x2, T.tda, T.lo_da, m0 - 2);
-      cmp_plane_if(ltA, gtA, x3, T.tda, T.lo_da, m0 - 3);
-    }
-  }
-  Masks r;
-  r.D = ltD;
-  r.A = ltA & ~ltD;
-  r.O = O;
-  return r;
-}
 
 // One window (a, b, c) for 32 samples (Alg. 1's tree on the bond the orientation picks,
 // written as bit logic like Alg. 2).  Lane with o=0: bond (a,b), fission target c; o=1: bond

@@ -276,3 +276,35 @@ def test_record_now_after_resume(P, oracle_mod):
     tot, _, _ = oracle_mod.run(st, p, d, seed, 0, subs[-1], subs)
     np.testing.assert_array_equal(c, tot)
     assert b.num_records == 3 and list(b.record_times()) == [7, 9, 12]
+
+
+def test_late_splice_deep_into_a_run(P, oracle_mod):
+    # 2^21 + 12345 sub-steps of the L=65536 lattice (1024 samples) on the specialised sweep,
+    # then three more sub-steps checked against the oracle started from the GPU state
+    L, S, p, d, seed = 65536, 1024, 0.15, 0.5, 1
+    n1 = (1 << 21) + 12345
+    sim = P.Pcpd(L, S, p, d, seed=seed, jit=1)
+    assert sim.plan()["jit"] == 1
+    sim.run_substeps(n1)
+    lat1 = sim.lattice()
+    sim.run_substeps(3)
+    lat2 = sim.lattice()
+    for g in (0, 13, 31):
+        st = oracle_mod.unpack(lat1[g:g + 1])
+        oracle_mod.run(st, p, d, seed, n1, n1 + 3, group0=g)
+        np.testing.assert_array_equal(lat2[g], oracle_mod.pack(st)[0], err_msg=f"group {g}")
+
+
+def test_substep_counter_near_its_limit(P, oracle_mod):
+    # the sub-step index is a 32-bit Philox counter word: a run may reach 2^32 - 1 and no further
+    L, S, p, d, seed = 600, 64, 0.2, 0.3, 5
+    n0 = (1 << 32) - 60
+    st0 = oracle_mod.init_state(L, S, INIT_HALF, seed)
+    sim = P.Pcpd(L, S, p, d, seed=seed)
+    sim.set_lattice(oracle_mod.pack(st0), n0)
+    sim.run_substeps(59)
+    st = st0.copy()
+    oracle_mod.run(st, p, d, seed, n0, n0 + 59)
+    np.testing.assert_array_equal(sim.lattice(), oracle_mod.pack(st))
+    with pytest.raises(P.PcpdError):
+        sim.run_substeps(2)
