@@ -59,6 +59,10 @@ def lib():
             L.orc_rs_run.argtypes = [C.c_uint32, C.c_uint32, C.c_uint64, C.c_uint64, C.c_uint64, u8p,
                                      C.c_uint64, C.c_uint64, u64p, C.c_uint32, u64p, u32p, C.c_int]
             L.orc_rs_run.restype = C.c_int
+            L.orc_paper_run.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
+                                        C.c_uint32, C.c_uint64, C.c_uint64, u8p, C.c_uint64, C.c_uint64,
+                                        u64p, C.c_uint32, u64p]
+            L.orc_paper_run.restype = C.c_int
             L.orc_pack.argtypes = [u8p, C.c_uint32, C.c_uint32, u32p]
             L.orc_unpack.argtypes = [u32p, C.c_uint32, C.c_uint32, u8p]
             _lib = L
@@ -163,3 +167,32 @@ def rs_run(state: np.ndarray, p: float, d: float, seed: int, a_begin: int, a_end
     if rc != 0:
         raise ValueError("oracle: bad arguments")
     return tot, ps
+
+
+def paper_thresholds(p: float, d: float, m: int, n_dec: int):
+    """(T_d, T_c) of the paper's scheme: d must be a multiple of 2^-m (T_d = d*2^m), and
+    p*2^n_dec <= 1 (T_c = floor(p*2^n_dec*2^32), 2^32 meaning always)."""
+    td = d * (1 << m)
+    if td != int(td) or not (0 <= td <= (1 << m)):
+        raise ValueError("d must be a multiple of 2^-m in [0, 1]")
+    c = p * float(1 << n_dec)
+    if not (0.0 <= c <= 1.0):
+        raise ValueError("need 0 <= p * 2^n_dec <= 1")
+    tc = min(1 << 32, int(np.floor(c * 4294967296.0)))
+    return int(td), tc
+
+
+def paper_run(state: np.ndarray, n_loc: int, S_w: int, p: float, d: float, m: int, n_dec: int,
+              seed: int, step_begin: int, step_end: int, rec_step=()):
+    """The paper's shared-local-site scheme (Sec. 3-4, Alg. 2) on ``state`` [systems][L]
+    bytes, L = 32*n_loc*S_w, in place.  Returns the record totals."""
+    st = state
+    assert st.dtype == np.uint8 and st.flags.c_contiguous and st.shape[1] == 32 * n_loc * S_w
+    td, tc = paper_thresholds(p, d, m, n_dec)
+    rec = np.ascontiguousarray(rec_step, dtype=np.uint64)
+    tot = np.zeros(len(rec), dtype=np.uint64)
+    rc = lib().orc_paper_run(n_loc, S_w, st.shape[0], m, td, n_dec, tc, C.c_uint64(seed), _p(st, C.c_uint8),
+                             step_begin, step_end, _p(rec, C.c_uint64), len(rec), _p(tot, C.c_uint64))
+    if rc != 0:
+        raise ValueError("oracle: bad arguments")
+    return tot

@@ -424,3 +424,84 @@ void orc_unpack(const uint32_t *words, uint32_t L, uint32_t S, uint8_t *state)
                 state[(uint64_t)(32u * g + j) * L + i] =
                     (uint8_t)((words[(uint64_t)g * L + i] >> j) & 1u);
 }
+
+/* ---------------------------------------------------------------------------------------
+ * The paper's own GPU scheme (Sec. 3-4, Alg. 2), as a variant.  One system (a lattice of
+ * L = 32 * n_loc * S_w sites) per workgroup of S_w workitems; bit b of workitem w's local
+ * word i holds site b*(L/32) + w*n_loc + i ("connected lattices", Sec. 4).  Every step
+ * draws one local site i* for the whole system and every workitem updates, for all 32 bits
+ * at once, the bond (s, s+1) with s = b*(L/32) + w*n_loc + i*, fission going to s-1 or s+2
+ * (all mod L).  Per workitem and step the random words, in stream order, are: m planes of
+ * the diffusion draw (bit b diffuses iff its m-bit value, MSB first, is below T_d =
+ * d*2^m), n_dec decorrelation words (ANDed), one word compared with T_c =
+ * floor(p*2^n_dec*2^32) and broadcast to all bits (the correlated annihilation draw), one
+ * fission-direction word (bit 1: high, s+2).  A bit annihilates iff no diffusion, an
+ * occupied pair, all decorrelation bits 1 and the broadcast draw true.  One step = 32*S_w
+ * attempts; MCS time t is step t*n_loc.
+ * Random words: block j of Philox counter (w, step, system, TAG_PAPER<<28 | j), words
+ * taken in order; the local site: floor(x0 * n_loc / 2^32) of (0, step, system,
+ * TAG_PAPER_SITE<<28).  state: bytes [systems][L].
+ * ------------------------------------------------------------------------------------- */
+#define ORC_TAG_PAPER 4u
+#define ORC_TAG_PAPER_SITE 5u
+
+int orc_paper_run(uint32_t n_loc, uint32_t S_w, uint32_t systems, uint32_t m, uint32_t t_d,
+                  uint32_t n_dec, uint64_t t_c, uint64_t seed, uint8_t *state, uint64_t step_begin,
+                  uint64_t step_end, const uint64_t *rec_step, uint32_t n_rec, uint64_t *rec_total)
+{
+    if (n_loc < 4 || S_w == 0 || m > 16 || (t_d >> m) > 1 || (t_d > (1u << m)) || n_dec > 16 ||
+        step_end > 0xFFFFFFFFull || step_end < step_begin)
+        return 1;
+    const uint64_t L = 32ull * n_loc * S_w;
+    const uint32_t nw = m + n_dec + 2;   /* words per workitem and step */
+    for (uint32_t r = 0; r < n_rec; ++r) rec_total[r] = 0;
+    uint32_t *words = (uint32_t *)calloc((size_t)nw + 4, sizeof(uint32_t));
+    for (uint32_t sys = 0; sys < systems; ++sys) {
+        uint8_t *q = state + (uint64_t)sys * L;
+        uint32_t r = 0;
+        while (r < n_rec && rec_step[r] < step_begin) ++r;
+        for (uint64_t st = step_begin;; ++st) {
+            while (r < n_rec && rec_step[r] == st) {
+                uint64_t c = 0;
+                for (uint64_t i = 0; i < L; ++i) c += q[i];
+                rec_total[r] += c;
+                ++r;
+            }
+            if (st == step_end) break;
+            uint32_t xs[4];
+            orc_block(seed, 0u, (uint32_t)st, sys, ORC_TAG_PAPER_SITE << 28, xs);
+            const uint32_t istar = (uint32_t)(((uint64_t)xs[0] * n_loc) >> 32);
+            for (uint32_t w = 0; w < S_w; ++w) {
+                for (uint32_t j = 0; 4 * j < nw; ++j)
+                    orc_block(seed, w, (uint32_t)st, sys, (ORC_TAG_PAPER << 28) | j, words + 4 * j);
+                const uint32_t corr = ((uint64_t)words[m + n_dec] < t_c) ? 1u : 0u;
+                const uint32_t fis = words[m + n_dec + 1];
+                for (uint32_t b = 0; b < 32; ++b) {
+                    uint32_t u = 0;
+                    for (uint32_t k = 0; k < m; ++k) u = (u << 1) | ((words[k] >> b) & 1u);
+                    const int diffuse = u < t_d;
+                    uint32_t dec = 1u;
+                    for (uint32_t k = 0; k < n_dec; ++k) dec &= (words[m + k] >> b) & 1u;
+                    const uint64_t s0 = (uint64_t)b * (L / 32) + (uint64_t)w * n_loc + istar;
+                    const uint64_t s1 = (s0 + 1) % L, sl = (s0 + L - 1) % L, sh = (s0 + 2) % L;
+                    if (diffuse) {
+                        uint8_t t = q[s0];
+                        q[s0] = q[s1];
+                        q[s1] = t;
+                    } else if (q[s0] && q[s1]) {
+                        if (dec && corr) {
+                            q[s0] = 0;
+                            q[s1] = 0;
+                        } else if ((fis >> b) & 1u) {
+                            q[sh] = 1;
+                        } else {
+                            q[sl] = 1;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    free(words);
+    return 0;
+}
