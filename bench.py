@@ -235,6 +235,54 @@ def stream_leg(pcpd, substeps: int = 2048):
             "hbm_gbs_algorithmic": hbm, "hbm_frac_of_measured_copy": hbm / 6787.2}
 
 
+def paper_ops_per_step_thread(m: int, n_dec: int) -> float:
+    """Algorithmic integer operations per (step, thread) of the paper's scheme: 40 per
+    Philox4x32-10 block (ceil((m + n_dec + 2)/4) mask blocks and 1/32 of a local-site block),
+    2 per diffusion plane, 1 per decorrelation word, 2 for the broadcast compare, 12 for the
+    bond logic of Alg. 2 and 8 shared-memory loads/stores.  One (step, thread) = 32 attempts."""
+    blocks = -(-(m + n_dec + 2) // 4) + 1.0 / 32.0
+    return 40.0 * blocks + 2.0 * m + n_dec + 2.0 + 12.0 + 8.0, blocks
+
+
+def paper_leg(pcpd, mcs: int = 200, systems: int = 4096):
+    """The paper's own scheme (Sec. 3-4, Alg. 2) at the layout it reports: rings of
+    L = 65536 sites (S_w = 64 threads x n_loc = 32 words, and S_w = 32 x 64), d = 1/2
+    (m = 1 plane), n_dec = 2 decorrelation words, p = 0.15, full start, `systems` systems,
+    20 log-spaced records; `mcs` MCS timed after 1 MCS of warm-up."""
+    import torch
+    out = []
+    m, n_dec = 1, 2
+    ops, blocks = paper_ops_per_step_thread(m, n_dec)
+    for n_loc, S_w in ((32, 64), (64, 32)):
+        L = 32 * n_loc * S_w
+        stream = torch.cuda.Stream()
+        h = pcpd.PaperScheme(n_loc, S_w, systems, 0.15, 0.5, m, n_dec, seed=1, stream=stream)
+        h.run(n_loc)
+        h.sync()
+        recs = sorted({n_loc * int(t) for t in log_times(mcs + 1, 20) if t > 1})
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        h.run(mcs * n_loc, recs)
+        ev1.record(stream)
+        h.sync()
+        ms = ev0.elapsed_time(ev1)
+        rate = systems * L * mcs / (ms / 1e3)
+        step_threads = rate / 32.0
+        out.append({"n_loc": n_loc, "S_w": S_w, "L": L, "systems": systems, "mcs": mcs,
+                    "value": rate, "unit": UNIT, "ms": ms, "plan": h.plan(),
+                    "rho_end": float(h.density()[-1]),
+                    "roofline": {"bound": "alu", "achieved": ops * step_threads / 1e12,
+                                 "peak": 40.27392, "unit": "Tops/s",
+                                 "frac": ops * step_threads / 40.27392e12,
+                                 "ops_per_step_thread": ops,
+                                 "frac_of_philox_pipe_cap": rate / (5.05e11 * 32.0 / blocks)}})
+        h.close()
+    return {"workload": "paper scheme, L=65536, %d systems, d=0.5 (m=1), n_dec=2, p=0.15, %d MCS"
+            % (systems, mcs), "runs": out,
+            "note": "a different Markov chain from the main path (shared local site, correlated "
+                    "annihilation draws); same unit as the paper's moves/s"}
+
+
 def serving_leg(pcpd, seconds: float = 8.0, mcs_scale: float = 1 / 600, rate_hz: float = 200.0):
     """Poisson request stream (200 req/s; L log-uniform 2^10..2^20, 64..4096 samples,
     p in [.05,.25], d in [.1,.9], MCS log-uniform 1e3..1e5) for `seconds` instead of 60 s and
@@ -305,6 +353,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-stream", action="store_true")
+    ap.add_argument("--no-paper", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -439,6 +488,7 @@ def main():
     batch = batch_leg(pcpd) if not args.no_batch else None
     serving = serving_leg(pcpd) if not args.no_serve else None
     streamed = stream_leg(pcpd) if not args.no_stream else None
+    paper = paper_leg(pcpd) if not args.no_paper else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -457,7 +507,7 @@ def main():
                            "l2": "inputs larger than L2: 3 lattices x 2 buffers x 32 MiB = 192 MiB, streamed per tile epoch",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-                "gpu_launches": launches, "batch": batch, "serving": serving, "streamed": streamed,
+                "gpu_launches": launches, "batch": batch, "serving": serving, "streamed": streamed, "paper_scheme": paper,
                 "paper_context": dict(PAPER_CONTEXT, this_run_over_paper_gpu=value / PAPER_CONTEXT["gpu_moves_per_s"])}
         print(json.dumps(line), flush=True)
     for s in sims:

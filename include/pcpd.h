@@ -285,6 +285,76 @@ int pcpd_server_get_stats(pcpd_server_t *sv, pcpd_server_stats *out);
 /* Stop the thread; requests not finished fail with "server stopped".  NULL-safe. */
 void pcpd_server_stop(pcpd_server_t *sv);
 
+/* ---- the paper's own GPU scheme (Sec. 3-4, Alg. 2), as a variant ----
+ * Kept beside the window schedule above so that both can be run and compared.  Each of
+ * `systems` independent systems is a ring of L = 32 * n_loc * S_w sites worked on by a group
+ * of S_w threads (the paper's workgroup of S_w workitems); the 32 bits of a word are 32
+ * segments of the same ring, L/32 sites apart ("connected lattices", Sec. 4).
+ * Layout of a system's lattice (host and device): uint32_t words[n_loc][S_w]; bit b of
+ * words[l][w] is site b*(L/32) + w*n_loc + l.  Systems follow one another.
+ * One step: a local site l* drawn for the whole system, then in every (w, b) the bond
+ * (s, s+1), s = b*(L/32) + w*n_loc + l*, is updated as in Alg. 2: the pair swaps with
+ * probability d; otherwise an occupied pair annihilates with probability p, else puts a
+ * particle on s+2 or s-1 with probability 1/2 each (all mod L).  One step = 32*S_w attempts
+ * per system; one MCS = n_loc steps.  The diffusion draw of a bit is an m-bit value compared
+ * with T_d = d*2^m (d must be a multiple of 2^-m, Sec. 4.2); the annihilation draw ANDs
+ * n_dec decorrelation words with one comparison against T_c = floor(p*2^n_dec*2^32) that is
+ * shared by all 32 bits of a word (the correlated draw with decorrelation of Sec. 4.3;
+ * p*2^n_dec <= 1).  Random words: Philox4x32-10 keyed by the seed, counted by
+ * (w, step, system, 4<<28 | block) for the masks and (0, step, system, 5<<28) for l*. */
+typedef struct pcpd_paper pcpd_paper_t;
+
+typedef struct pcpd_paper_params {
+    uint32_t n_loc;      /* local words per thread, >= 4 */
+    uint32_t S_w;        /* threads per system, a multiple of 32 in [32, 1024] */
+    uint32_t systems;    /* independent systems, 1 .. 2^24 */
+    double p;            /* annihilation probability, 0 <= p*2^n_dec <= 1 */
+    double d;            /* diffusion probability, a multiple of 2^-m in [0, 1] */
+    uint32_t m;          /* diffusion planes, 0 .. 16 */
+    uint32_t n_dec;      /* decorrelation words, 0 .. 16 */
+    uint64_t seed;       /* Philox key */
+    int init;            /* PCPD_INIT_FULL (0) or PCPD_INIT_EMPTY */
+    void *stream;        /* cudaStream_t; NULL = a stream owned by the handle */
+    uint32_t plan_spc;   /* systems per CTA (0 = automatic; changes no result bit) */
+    int generic;         /* non-zero: run the kernel that reads m and n_dec at run time
+                            (same bits; for tests) */
+} pcpd_paper_params;
+
+/* T_d = d*2^m and T_c = min(2^32, floor(p*2^n_dec*2^32)) (IEEE double); PCPD_EINVAL if d is
+ * not a multiple of 2^-m, p*2^n_dec is outside [0, 1], or m or n_dec exceeds 16. */
+int pcpd_paper_thresholds(double p, double d, uint32_t m, uint32_t n_dec, uint32_t *t_d,
+                          uint64_t *t_c);
+
+/* Create: every system's lattice resides in one CTA's shared memory during a launch, so
+ * n_loc*S_w*4 bytes must fit (about 227 KB: L up to ~1.8e6 sites).  Device lattice
+ * systems*n_loc*S_w words, filled (FULL) or empty. */
+int pcpd_paper_create(const pcpd_paper_params *prm, pcpd_paper_t **out);
+
+/* Advance every system by n_steps steps and record the occupied sites (summed over systems,
+ * and per system) at each absolute step in record_steps[0..n_rec): strictly increasing, in
+ * (now, now + n_steps]; the current step is allowed as the first entry.  The final step
+ * count must stay below 2^32.  Enqueued on the handle's stream (copies record_steps first). */
+int pcpd_paper_run(pcpd_paper_t *h, uint64_t n_steps, const uint64_t *record_steps, size_t n_rec);
+
+size_t pcpd_paper_num_records(const pcpd_paper_t *h);
+uint64_t pcpd_paper_step(const pcpd_paper_t *h);
+
+/* First n records: counts_out[n] (sum over systems, nullable) and per_system_out[n][systems]
+ * (nullable).  Waits. */
+int pcpd_paper_counts(const pcpd_paper_t *h, uint64_t *counts_out, uint32_t *per_system_out, size_t n);
+
+/* Copy the lattice (systems*n_loc*S_w words, layout above) out / in.  set_lattice also sets
+ * the step counter and clears the records.  Both wait. */
+int pcpd_paper_get_lattice(const pcpd_paper_t *h, uint32_t *host_out);
+int pcpd_paper_set_lattice(pcpd_paper_t *h, const uint32_t *host_in, uint64_t step);
+
+/* Launch shape: systems per CTA, threads per CTA, CTAs, dynamic shared memory per CTA. */
+int pcpd_paper_get_plan(const pcpd_paper_t *h, uint32_t *systems_per_cta, uint32_t *threads,
+                        uint32_t *grid, size_t *smem_bytes);
+
+int pcpd_paper_sync(pcpd_paper_t *h);
+void pcpd_paper_destroy(pcpd_paper_t *h);
+
 /* ---- allocation-free sweep ----
  * Advance a caller-owned lattice by n_substeps sub-steps without allocating any memory.
  * The paper has no counterpart: this is an entry point for callers that cannot let a

@@ -61,7 +61,7 @@ def lib():
             L.orc_rs_run.restype = C.c_int
             L.orc_paper_run.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
                                         C.c_uint32, C.c_uint64, C.c_uint64, u8p, C.c_uint64, C.c_uint64,
-                                        u64p, C.c_uint32, u64p]
+                                        u64p, C.c_uint32, u64p, C.c_uint32, u32p]
             L.orc_paper_run.restype = C.c_int
             L.orc_pack.argtypes = [u8p, C.c_uint32, C.c_uint32, u32p]
             L.orc_unpack.argtypes = [u32p, C.c_uint32, C.c_uint32, u8p]
@@ -183,16 +183,20 @@ def paper_thresholds(p: float, d: float, m: int, n_dec: int):
 
 
 def paper_run(state: np.ndarray, n_loc: int, S_w: int, p: float, d: float, m: int, n_dec: int,
-              seed: int, step_begin: int, step_end: int, rec_step=()):
+              seed: int, step_begin: int, step_end: int, rec_step=(), sys0: int = 0,
+              per_system: bool = False):
     """The paper's shared-local-site scheme (Sec. 3-4, Alg. 2) on ``state`` [systems][L]
-    bytes, L = 32*n_loc*S_w, in place.  Returns the record totals."""
+    bytes (systems sys0, sys0+1, ...), L = 32*n_loc*S_w, in place.  Returns the record
+    totals, and the per-system counts [n_rec][systems] when ``per_system``."""
     st = state
     assert st.dtype == np.uint8 and st.flags.c_contiguous and st.shape[1] == 32 * n_loc * S_w
     td, tc = paper_thresholds(p, d, m, n_dec)
     rec = np.ascontiguousarray(rec_step, dtype=np.uint64)
     tot = np.zeros(len(rec), dtype=np.uint64)
+    ps = np.zeros((len(rec), st.shape[0]), dtype=np.uint32)
     rc = lib().orc_paper_run(n_loc, S_w, st.shape[0], m, td, n_dec, tc, C.c_uint64(seed), _p(st, C.c_uint8),
-                             step_begin, step_end, _p(rec, C.c_uint64), len(rec), _p(tot, C.c_uint64))
+                             step_begin, step_end, _p(rec, C.c_uint64), len(rec), _p(tot, C.c_uint64),
+                             sys0, _p(ps, C.c_uint32))
     if rc != 0:
         raise ValueError("oracle: bad arguments")
-    return tot
+    return (tot, ps) if per_system else tot

@@ -440,14 +440,16 @@ void orc_unpack(const uint32_t *words, uint32_t L, uint32_t S, uint8_t *state)
  * attempts; MCS time t is step t*n_loc.
  * Random words: block j of Philox counter (w, step, system, TAG_PAPER<<28 | j), words
  * taken in order; the local site: floor(x0 * n_loc / 2^32) of (0, step, system,
- * TAG_PAPER_SITE<<28).  state: bytes [systems][L].
+ * TAG_PAPER_SITE<<28).  state: bytes [systems][L] of systems sys0, sys0+1, ...;
+ * rec_sys (nullable): per-system counts [n_rec][systems].
  * ------------------------------------------------------------------------------------- */
 #define ORC_TAG_PAPER 4u
 #define ORC_TAG_PAPER_SITE 5u
 
 int orc_paper_run(uint32_t n_loc, uint32_t S_w, uint32_t systems, uint32_t m, uint32_t t_d,
                   uint32_t n_dec, uint64_t t_c, uint64_t seed, uint8_t *state, uint64_t step_begin,
-                  uint64_t step_end, const uint64_t *rec_step, uint32_t n_rec, uint64_t *rec_total)
+                  uint64_t step_end, const uint64_t *rec_step, uint32_t n_rec, uint64_t *rec_total,
+                  uint32_t sys0, uint32_t *rec_sys)
 {
     if (n_loc < 4 || S_w == 0 || m > 16 || (t_d >> m) > 1 || (t_d > (1u << m)) || n_dec > 16 ||
         step_end > 0xFFFFFFFFull || step_end < step_begin)
@@ -465,15 +467,16 @@ int orc_paper_run(uint32_t n_loc, uint32_t S_w, uint32_t systems, uint32_t m, ui
                 uint64_t c = 0;
                 for (uint64_t i = 0; i < L; ++i) c += q[i];
                 rec_total[r] += c;
+                if (rec_sys) rec_sys[(uint64_t)r * systems + sys] = (uint32_t)c;
                 ++r;
             }
             if (st == step_end) break;
             uint32_t xs[4];
-            orc_block(seed, 0u, (uint32_t)st, sys, ORC_TAG_PAPER_SITE << 28, xs);
+            orc_block(seed, 0u, (uint32_t)st, sys0 + sys, ORC_TAG_PAPER_SITE << 28, xs);
             const uint32_t istar = (uint32_t)(((uint64_t)xs[0] * n_loc) >> 32);
             for (uint32_t w = 0; w < S_w; ++w) {
                 for (uint32_t j = 0; 4 * j < nw; ++j)
-                    orc_block(seed, w, (uint32_t)st, sys, (ORC_TAG_PAPER << 28) | j, words + 4 * j);
+                    orc_block(seed, w, (uint32_t)st, sys0 + sys, (ORC_TAG_PAPER << 28) | j, words + 4 * j);
                 const uint32_t corr = ((uint64_t)words[m + n_dec] < t_c) ? 1u : 0u;
                 const uint32_t fis = words[m + n_dec + 1];
                 for (uint32_t b = 0; b < 32; ++b) {

@@ -10,6 +10,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libpcpd.so")
 SOURCES = [os.path.join(CSRC, "pcpd_capi.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, "pcpd_kernels.cuh"), os.path.join(CSRC, "pcpd_engine.cuh"),
+                  os.path.join(CSRC, "pcpd_paper.cuh"),
                   os.path.join(CSRC, "pcpd_jit_src.inc"),
                   os.path.join(os.path.dirname(HERE), "include", "pcpd.h")]
 

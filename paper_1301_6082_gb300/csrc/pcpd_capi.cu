@@ -27,6 +27,7 @@
 
 #include "../../include/pcpd.h"
 #include "pcpd_engine.cuh"
+#include "pcpd_paper.cuh"
 
 namespace {
 
@@ -1840,5 +1841,306 @@ extern "C" int pcpd_autotune(const pcpd_params *prm, uint32_t trial_substeps, pc
   const TunedPlan t{win.threads, win.seg, win.tau, best_r};
   g_tune[{prm->L, prm->samples}] = t;
   tune_file_append(prm->L, prm->samples, t);
+  return PCPD_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// The paper's own GPU scheme (Sec. 3-4, Alg. 2) as a variant: one system per group of S_w
+// threads, a shared random local site per step, correlated annihilation draws.
+struct pcpd_paper {
+  uint32_t n_loc = 0, S_w = 0, systems = 0, L = 0, words = 0;
+  uint32_t m = 0, n_dec = 0, t_d = 0, d_full = 0, tc = 0, tc_full = 0;
+  pcpdk::RoundKeys rk{};
+  uint64_t step = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  uint32_t *d_lat = nullptr;
+  std::vector<uint64_t> rec_steps;
+  unsigned long long *d_rec_total = nullptr, *d_rec_step = nullptr;
+  uint32_t *d_rec_sys = nullptr;
+  size_t rec_cap = 0;
+  uint32_t spc = 1, threads = 0, grid = 0;
+  size_t smem = 0;
+  void (*kernel)(const pcpdk::PaperParams) = nullptr;
+};
+
+namespace {
+
+using PaperKernel = void (*)(const pcpdk::PaperParams);
+
+// Compile-time plane/decorrelation counts for the common cases, a generic kernel otherwise.
+template <int M>
+PaperKernel paper_kernel_m(uint32_t nd) {
+  switch (nd) {
+    case 0: return pcpdk::k_paper_sweep<M, 0>;
+    case 1: return pcpdk::k_paper_sweep<M, 1>;
+    case 2: return pcpdk::k_paper_sweep<M, 2>;
+    case 3: return pcpdk::k_paper_sweep<M, 3>;
+    default: return pcpdk::k_paper_sweep<-1, 0>;
+  }
+}
+
+PaperKernel paper_kernel(uint32_t m, uint32_t nd, int generic) {
+  if (generic) return pcpdk::k_paper_sweep<-1, 0>;
+  switch (m) {
+    case 0: return paper_kernel_m<0>(nd);
+    case 1: return paper_kernel_m<1>(nd);
+    case 2: return paper_kernel_m<2>(nd);
+    case 3: return paper_kernel_m<3>(nd);
+    default: return pcpdk::k_paper_sweep<-1, 0>;
+  }
+}
+
+// Raise a kernel's dynamic shared-memory limit once per process (the attribute is global).
+int paper_smem_optin(PaperKernel k, size_t bytes) {
+  static std::mutex mu;
+  static std::vector<std::pair<const void *, size_t>> done;
+  std::lock_guard<std::mutex> lk(mu);
+  for (auto &e : done)
+    if (e.first == (const void *)k && e.second >= bytes) return PCPD_OK;
+  int optin = 0;
+  int rc = smem_optin(&optin);
+  if (rc) return rc;
+  CU(cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  done.emplace_back((const void *)k, (size_t)optin);
+  return PCPD_OK;
+}
+
+int paper_ensure_records(pcpd_paper_t *h, size_t need) {
+  if (need <= h->rec_cap) return PCPD_OK;
+  size_t cap = h->rec_cap ? h->rec_cap : 64;
+  while (cap < need) cap *= 2;
+  unsigned long long *nt = nullptr, *ns = nullptr;
+  uint32_t *nsys = nullptr;
+  CU(cudaMalloc(&nt, cap * sizeof(unsigned long long)));
+  CU(cudaMalloc(&ns, cap * sizeof(unsigned long long)));
+  CU(cudaMalloc(&nsys, cap * (size_t)h->systems * sizeof(uint32_t)));
+  CU(cudaMemsetAsync(nt, 0, cap * sizeof(unsigned long long), h->stream));
+  CU(cudaMemsetAsync(nsys, 0, cap * (size_t)h->systems * sizeof(uint32_t), h->stream));
+  const size_t have = h->rec_steps.size();
+  if (have) {
+    CU(cudaMemcpyAsync(nt, h->d_rec_total, have * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, h->stream));
+    CU(cudaMemcpyAsync(nsys, h->d_rec_sys, have * (size_t)h->systems * sizeof(uint32_t),
+                       cudaMemcpyDeviceToDevice, h->stream));
+  }
+  CU(cudaStreamSynchronize(h->stream));
+  cudaFree(h->d_rec_total);
+  cudaFree(h->d_rec_step);
+  cudaFree(h->d_rec_sys);
+  h->d_rec_total = nt;
+  h->d_rec_step = ns;
+  h->d_rec_sys = nsys;
+  h->rec_cap = cap;
+  return PCPD_OK;
+}
+
+}  // namespace
+
+int pcpd_paper_thresholds(double p, double d, uint32_t m, uint32_t n_dec, uint32_t *t_d,
+                          uint64_t *t_c) {
+  if (!t_d || !t_c) return fail(PCPD_EINVAL, "NULL output");
+  if (m > 16 || n_dec > 16) return fail(PCPD_EINVAL, "m and n_dec must be at most 16 (m=%u, n_dec=%u)", m, n_dec);
+  const double td = d * (double)(1u << m);
+  if (!(td >= 0.0 && td <= (double)(1u << m)) || td != std::floor(td))
+    return fail(PCPD_EINVAL, "d=%g is not a multiple of 2^-%u in [0, 1]", d, m);
+  const double c = p * (double)(1u << n_dec);
+  if (!(c >= 0.0 && c <= 1.0)) return fail(PCPD_EINVAL, "need 0 <= p * 2^n_dec <= 1 (p=%g, n_dec=%u)", p, n_dec);
+  *t_d = (uint32_t)td;
+  *t_c = floor_scaled(c * 4294967296.0);
+  return PCPD_OK;
+}
+
+int pcpd_paper_create(const pcpd_paper_params *prm, pcpd_paper_t **out) {
+  if (!prm || !out) return fail(PCPD_EINVAL, "NULL argument");
+  *out = nullptr;
+  if (prm->n_loc < 4) return fail(PCPD_EINVAL, "n_loc must be at least 4 (n_loc=%u)", prm->n_loc);
+  if (prm->S_w < 32 || prm->S_w > 1024 || prm->S_w % 32)
+    return fail(PCPD_EINVAL, "S_w must be a multiple of 32 in [32, 1024] (S_w=%u)", prm->S_w);
+  if (prm->systems == 0 || prm->systems > (1u << 24))
+    return fail(PCPD_EINVAL, "systems must lie in [1, 2^24] (systems=%u)", prm->systems);
+  if (prm->init != PCPD_INIT_FULL && prm->init != PCPD_INIT_EMPTY)
+    return fail(PCPD_EINVAL, "init must be PCPD_INIT_FULL or PCPD_INIT_EMPTY (init=%d)", prm->init);
+  uint32_t t_d = 0;
+  uint64_t t_c = 0;
+  int rc = pcpd_paper_thresholds(prm->p, prm->d, prm->m, prm->n_dec, &t_d, &t_c);
+  if (rc) return rc;
+  rc = device_check();
+  if (rc) return rc;
+  int optin = 0;
+  rc = smem_optin(&optin);
+  if (rc) return rc;
+  const uint64_t words = (uint64_t)prm->n_loc * prm->S_w;
+  if (words * 4 > (uint64_t)optin)
+    return fail(PCPD_EINVAL, "a system of n_loc*S_w = %llu words does not fit one CTA's shared memory (%d bytes)",
+                (unsigned long long)words, optin);
+  uint32_t spc = prm->plan_spc;
+  if (spc == 0) {
+    spc = prm->S_w >= 256 ? 1u : 256u / prm->S_w;
+    while (spc > 1 && spc * words * 4 > (uint64_t)optin) --spc;
+  }
+  if (spc > 15 || spc * prm->S_w > 1024 || spc * words * 4 > (uint64_t)optin)
+    return fail(PCPD_EINVAL, "plan_spc=%u systems per CTA does not fit (at most 15, 1024 threads, %d bytes)", spc, optin);
+
+  pcpd_paper_t *h = new pcpd_paper();
+  auto bail = [&](int code) {
+    pcpd_paper_destroy(h);
+    return code;
+  };
+  h->n_loc = prm->n_loc;
+  h->S_w = prm->S_w;
+  h->systems = prm->systems;
+  h->words = (uint32_t)words;
+  h->L = 32u * h->words;
+  h->m = prm->m;
+  h->n_dec = prm->n_dec;
+  h->t_d = t_d;
+  h->d_full = t_d == (1u << prm->m) ? 1u : 0u;
+  h->tc = (uint32_t)(t_c & 0xFFFFFFFFull);
+  h->tc_full = t_c >= kTwo32 ? 1u : 0u;
+  h->rk = pcpdk::make_round_keys((uint32_t)(prm->seed & 0xFFFFFFFFu), (uint32_t)(prm->seed >> 32));
+  h->spc = spc;
+  h->threads = spc * h->S_w;
+  h->grid = (h->systems + spc - 1) / spc;
+  h->smem = (size_t)spc * words * 4;
+  h->kernel = paper_kernel(h->m, h->n_dec, prm->generic);
+  rc = paper_smem_optin(h->kernel, h->smem);
+  if (rc) return bail(rc);
+  if (prm->stream) {
+    h->stream = (cudaStream_t)prm->stream;
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(fail(PCPD_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e)));
+    h->own_stream = true;
+  }
+  const size_t bytes = (size_t)h->systems * words * 4;
+  cudaError_t e = cudaMalloc(&h->d_lat, bytes);
+  if (e != cudaSuccess) return bail(fail(PCPD_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e)));
+  e = cudaMemsetAsync(h->d_lat, prm->init == PCPD_INIT_FULL ? 0xFF : 0x00, bytes, h->stream);
+  if (e != cudaSuccess) return bail(fail(PCPD_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e)));
+  *out = h;
+  return PCPD_OK;
+}
+
+void pcpd_paper_destroy(pcpd_paper_t *h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  cudaFree(h->d_lat);
+  cudaFree(h->d_rec_total);
+  cudaFree(h->d_rec_step);
+  cudaFree(h->d_rec_sys);
+  if (h->own_stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+int pcpd_paper_run(pcpd_paper_t *h, uint64_t n_steps, const uint64_t *record_steps, size_t n_rec) {
+  if (!h) return fail(PCPD_EINVAL, "NULL handle");
+  if (n_rec && !record_steps) return fail(PCPD_EINVAL, "record_steps is NULL");
+  const uint64_t end = h->step + n_steps;
+  if (end > 0xFFFFFFFFull) return fail(PCPD_EINVAL, "step count %llu would exceed 2^32 - 1", (unsigned long long)end);
+  for (size_t i = 0; i < n_rec; ++i) {
+    const uint64_t s = record_steps[i];
+    if (i && s <= record_steps[i - 1]) return fail(PCPD_EINVAL, "record steps must be strictly increasing");
+    if (s > end || s < h->step || (s == h->step && i != 0))
+      return fail(PCPD_EINVAL, "record step %llu outside [%llu, %llu] (the current step only as the first)",
+                  (unsigned long long)s, (unsigned long long)h->step, (unsigned long long)end);
+  }
+  const size_t slot0 = h->rec_steps.size();
+  int rc = paper_ensure_records(h, slot0 + n_rec);
+  if (rc) return rc;
+  if (n_rec) {
+    CU(cudaMemcpyAsync(h->d_rec_step + slot0, record_steps, n_rec * sizeof(uint64_t), cudaMemcpyHostToDevice,
+                       h->stream));
+    CU(cudaStreamSynchronize(h->stream));  // record_steps belongs to the caller
+  }
+  // launches of at most 2^20 steps; a launch records the steps in [a, b), the last one also b
+  constexpr uint64_t kChunk = 1ull << 20;
+  size_t r = 0;
+  uint64_t a = h->step;
+  do {
+    const uint64_t b = std::min(end, a + kChunk);
+    size_t r1 = r;
+    while (r1 < n_rec && (record_steps[r1] < b || (b == end && record_steps[r1] == b))) ++r1;
+    pcpdk::PaperParams P{};
+    P.lat = h->d_lat;
+    P.rec_step = h->d_rec_step + slot0 + r;
+    P.rec_total = h->d_rec_total + slot0 + r;
+    P.rec_sys = h->d_rec_sys + (slot0 + r) * (size_t)h->systems;
+    P.rk = h->rk;
+    P.n_loc = h->n_loc;
+    P.S_w = h->S_w;
+    P.systems = h->systems;
+    P.spc = h->spc;
+    P.m = h->m;
+    P.t_d = h->t_d;
+    P.d_full = h->d_full;
+    P.n_dec = h->n_dec;
+    P.tc = h->tc;
+    P.tc_full = h->tc_full;
+    P.step_begin = (uint32_t)a;
+    P.step_end = (uint32_t)b;
+    P.n_rec = (uint32_t)(r1 - r);
+    P.systems_total = h->systems;
+    h->kernel<<<h->grid, h->threads, h->smem, h->stream>>>(P);
+    CU(cudaGetLastError());
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    r = r1;
+    a = b;
+  } while (a < end);
+  h->rec_steps.insert(h->rec_steps.end(), record_steps, record_steps + n_rec);
+  h->step = end;
+  return PCPD_OK;
+}
+
+size_t pcpd_paper_num_records(const pcpd_paper_t *h) { return h ? h->rec_steps.size() : 0; }
+
+uint64_t pcpd_paper_step(const pcpd_paper_t *h) { return h ? h->step : 0; }
+
+int pcpd_paper_counts(const pcpd_paper_t *h, uint64_t *counts_out, uint32_t *per_system_out, size_t n) {
+  if (!h) return fail(PCPD_EINVAL, "NULL handle");
+  if (n > h->rec_steps.size()) return fail(PCPD_EINVAL, "only %zu records taken", h->rec_steps.size());
+  if (n == 0) return PCPD_OK;
+  if (counts_out)
+    CU(cudaMemcpyAsync(counts_out, h->d_rec_total, n * sizeof(uint64_t), cudaMemcpyDeviceToHost, h->stream));
+  if (per_system_out)
+    CU(cudaMemcpyAsync(per_system_out, h->d_rec_sys, n * (size_t)h->systems * sizeof(uint32_t),
+                       cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  return PCPD_OK;
+}
+
+int pcpd_paper_get_lattice(const pcpd_paper_t *h, uint32_t *host_out) {
+  if (!h || !host_out) return fail(PCPD_EINVAL, "NULL argument");
+  CU(cudaMemcpyAsync(host_out, h->d_lat, (size_t)h->systems * h->words * 4, cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  return PCPD_OK;
+}
+
+int pcpd_paper_set_lattice(pcpd_paper_t *h, const uint32_t *host_in, uint64_t step) {
+  if (!h || !host_in) return fail(PCPD_EINVAL, "NULL argument");
+  if (step > 0xFFFFFFFFull) return fail(PCPD_EINVAL, "step must be < 2^32");
+  CU(cudaMemcpyAsync(h->d_lat, host_in, (size_t)h->systems * h->words * 4, cudaMemcpyHostToDevice, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  h->step = step;
+  h->rec_steps.clear();
+  if (h->d_rec_total) {
+    CU(cudaMemsetAsync(h->d_rec_total, 0, h->rec_cap * sizeof(unsigned long long), h->stream));
+    CU(cudaMemsetAsync(h->d_rec_sys, 0, h->rec_cap * (size_t)h->systems * sizeof(uint32_t), h->stream));
+  }
+  return PCPD_OK;
+}
+
+int pcpd_paper_get_plan(const pcpd_paper_t *h, uint32_t *systems_per_cta, uint32_t *threads,
+                        uint32_t *grid, size_t *smem_bytes) {
+  if (!h) return fail(PCPD_EINVAL, "NULL handle");
+  if (systems_per_cta) *systems_per_cta = h->spc;
+  if (threads) *threads = h->threads;
+  if (grid) *grid = h->grid;
+  if (smem_bytes) *smem_bytes = h->smem;
+  return PCPD_OK;
+}
+
+int pcpd_paper_sync(pcpd_paper_t *h) {
+  if (!h) return fail(PCPD_EINVAL, "NULL handle");
+  CU(cudaStreamSynchronize(h->stream));
   return PCPD_OK;
 }

@@ -53,6 +53,12 @@ class ServerStats(C.Structure):
                 ("active", C.c_uint64), ("queued", C.c_uint64), ("mem_used_bytes", C.c_size_t)]
 
 
+class PaperParams(C.Structure):
+    _fields_ = [("n_loc", C.c_uint32), ("S_w", C.c_uint32), ("systems", C.c_uint32), ("p", C.c_double),
+                ("d", C.c_double), ("m", C.c_uint32), ("n_dec", C.c_uint32), ("seed", C.c_uint64),
+                ("init", C.c_int), ("stream", C.c_void_p), ("plan_spc", C.c_uint32), ("generic", C.c_int)]
+
+
 # (name, restype, argtypes) of every exported entry point in include/pcpd.h
 SIGNATURES = [
     ("pcpd_create", C.c_void_p, [C.c_uint32, C.c_uint32, C.c_double, C.c_double, C.c_uint64]),
@@ -95,6 +101,17 @@ SIGNATURES = [
     ("pcpd_server_wait_idle", C.c_int, [C.c_void_p]),
     ("pcpd_server_get_stats", C.c_int, [C.c_void_p, C.POINTER(ServerStats)]),
     ("pcpd_server_stop", None, [C.c_void_p]),
+    ("pcpd_paper_thresholds", C.c_int, [C.c_double, C.c_double, C.c_uint32, C.c_uint32, _u32p, _u64p]),
+    ("pcpd_paper_create", C.c_int, [C.POINTER(PaperParams), C.POINTER(C.c_void_p)]),
+    ("pcpd_paper_run", C.c_int, [C.c_void_p, C.c_uint64, _u64p, C.c_size_t]),
+    ("pcpd_paper_num_records", C.c_size_t, [C.c_void_p]),
+    ("pcpd_paper_step", C.c_uint64, [C.c_void_p]),
+    ("pcpd_paper_counts", C.c_int, [C.c_void_p, _u64p, _u32p, C.c_size_t]),
+    ("pcpd_paper_get_lattice", C.c_int, [C.c_void_p, _u32p]),
+    ("pcpd_paper_set_lattice", C.c_int, [C.c_void_p, _u32p, C.c_uint64]),
+    ("pcpd_paper_get_plan", C.c_int, [C.c_void_p, _u32p, _u32p, _u32p, C.POINTER(C.c_size_t)]),
+    ("pcpd_paper_sync", C.c_int, [C.c_void_p]),
+    ("pcpd_paper_destroy", None, [C.c_void_p]),
     ("pcpd_sweep_noalloc", C.c_int, [C.c_void_p, C.c_void_p, C.c_uint32, C.c_uint32, C.c_double, C.c_double,
                                      C.c_uint64, C.c_uint64, C.c_uint64, C.c_void_p]),
 ]
@@ -412,3 +429,93 @@ def sweep_noalloc(lat_in_dev, lat_out_dev, L: int, samples: int, p: float, d: fl
     s = C.c_void_p(int(getattr(stream, "cuda_stream", 0) or 0)) if stream is not None else None
     _check(load().pcpd_sweep_noalloc(C.c_void_p(lat_in_dev.data_ptr()), C.c_void_p(lat_out_dev.data_ptr()),
                                      L, samples, p, d, seed, substep_begin, n_substeps, s))
+
+
+def paper_thresholds(p: float, d: float, m: int, n_dec: int):
+    """(T_d, T_c) of the paper's scheme (see include/pcpd.h)."""
+    td, tc = C.c_uint32(), C.c_uint64()
+    _check(load().pcpd_paper_thresholds(p, d, m, n_dec, C.byref(td), C.byref(tc)))
+    return int(td.value), int(tc.value)
+
+
+class PaperScheme:
+    """The paper's own GPU scheme (Sec. 3-4, Alg. 2): `systems` independent rings of
+    L = 32*n_loc*S_w sites, one group of S_w threads each, a shared random local site per
+    step, dyadic diffusion masks and correlated annihilation draws with n_dec decorrelation
+    words.  Lattice layout: words [systems][n_loc][S_w]; bit b of [s][l][w] is site
+    b*(L/32) + w*n_loc + l.  Time in steps: one MCS = n_loc steps."""
+
+    def __init__(self, n_loc: int, S_w: int, systems: int, p: float, d: float, m: int = 1,
+                 n_dec: int = 2, seed: int = 1, init: int = INIT_FULL, stream=None,
+                 plan_spc: int = 0, generic: bool = False):
+        lib = load()
+        prm = PaperParams()
+        prm.n_loc, prm.S_w, prm.systems, prm.p, prm.d = n_loc, S_w, systems, p, d
+        prm.m, prm.n_dec, prm.seed, prm.init = m, n_dec, seed, init
+        prm.plan_spc, prm.generic = plan_spc, 1 if generic else 0
+        if stream is not None:
+            prm.stream = C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+        h = C.c_void_p()
+        _check(lib.pcpd_paper_create(C.byref(prm), C.byref(h)))
+        self._h = h
+        self.n_loc, self.S_w, self.systems = n_loc, S_w, systems
+        self.L = 32 * n_loc * S_w
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().pcpd_paper_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def run(self, n_steps: int, record_steps=()):
+        r = np.ascontiguousarray(record_steps, dtype=np.uint64)
+        _check(load().pcpd_paper_run(self._h, n_steps, _ptr(r, C.c_uint64) if r.size else None, r.size))
+
+    @property
+    def step(self) -> int:
+        return int(load().pcpd_paper_step(self._h))
+
+    @property
+    def num_records(self) -> int:
+        return int(load().pcpd_paper_num_records(self._h))
+
+    def counts(self, per_system: bool = False):
+        n = self.num_records
+        c = np.zeros(n, dtype=np.uint64)
+        ps = np.zeros((n, self.systems), dtype=np.uint32) if per_system else None
+        if n:
+            _check(load().pcpd_paper_counts(self._h, _ptr(c, C.c_uint64),
+                                            _ptr(ps, C.c_uint32) if ps is not None else None, n))
+        return (c, ps) if per_system else c
+
+    def density(self) -> np.ndarray:
+        return self.counts() / float(self.L * self.systems)
+
+    def lattice(self) -> np.ndarray:
+        out = np.zeros((self.systems, self.n_loc, self.S_w), dtype=np.uint32)
+        _check(load().pcpd_paper_get_lattice(self._h, _ptr(out, C.c_uint32)))
+        return out
+
+    def set_lattice(self, words: np.ndarray, step: int):
+        w = np.ascontiguousarray(words, dtype=np.uint32)
+        assert w.shape == (self.systems, self.n_loc, self.S_w)
+        _check(load().pcpd_paper_set_lattice(self._h, _ptr(w, C.c_uint32), step))
+
+    def plan(self) -> dict:
+        a, b, c, s = C.c_uint32(), C.c_uint32(), C.c_uint32(), C.c_size_t()
+        _check(load().pcpd_paper_get_plan(self._h, C.byref(a), C.byref(b), C.byref(c), C.byref(s)))
+        return {"systems_per_cta": a.value, "threads": b.value, "grid": c.value, "smem_bytes": s.value}
+
+    def sync(self):
+        _check(load().pcpd_paper_sync(self._h))

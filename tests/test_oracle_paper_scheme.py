@@ -65,3 +65,18 @@ def test_paper_thresholds_checks(oracle_mod):
         oracle_mod.paper_thresholds(0.3, 0.5, 1, 2)     # p * 4 > 1
     with pytest.raises(ValueError):
         oracle_mod.paper_thresholds(0.1, 0.3, 2, 0)     # 0.3 is not a multiple of 1/4
+
+
+def test_system_offset_and_per_system_counts(oracle_mod):
+    # systems are independent streams: running them together equals running each at its offset
+    rng = np.random.default_rng(3)
+    st = (rng.random((4, 32 * 4 * 32)) < 0.6).astype(np.uint8)
+    parts = st.copy()
+    tot, ps = oracle_mod.paper_run(st, 4, 32, 0.2, 0.5, 1, 2, 9, 5, 60, [5, 30, 60], per_system=True)
+    for s in range(4):
+        one = np.ascontiguousarray(parts[s:s + 1])
+        t1 = oracle_mod.paper_run(one, 4, 32, 0.2, 0.5, 1, 2, 9, 5, 60, [5, 30, 60], sys0=s)
+        np.testing.assert_array_equal(one[0], st[s])
+        np.testing.assert_array_equal(t1, ps[:, s])
+    np.testing.assert_array_equal(ps.sum(1), tot)
+    np.testing.assert_array_equal(ps[-1], st.sum(1))
