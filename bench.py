@@ -237,18 +237,20 @@ def stream_leg(pcpd, substeps: int = 2048):
 
 def paper_ops_per_step_thread(m: int, n_dec: int) -> float:
     """Algorithmic integer operations per (step, thread) of the paper's scheme: 40 per
-    Philox4x32-10 block (ceil((m + n_dec + 2)/4) mask blocks and 1/32 of a local-site block),
-    2 per diffusion plane, 1 per decorrelation word, 2 for the broadcast compare, 12 for the
-    bond logic of Alg. 2 and 8 shared-memory loads/stores.  One (step, thread) = 32 attempts."""
-    blocks = -(-(m + n_dec + 2) // 4) + 1.0 / 32.0
+    Philox4x32-10 block ((m + n_dec + 2)/4 mask blocks, as four steps share whole blocks, and
+    1/128 of a local-site block), 2 per diffusion plane, 1 per decorrelation word, 2 for the
+    broadcast compare, 12 for the bond logic of Alg. 2 and 8 shared-memory loads/stores.
+    One (step, thread) = 32 attempts."""
+    blocks = (m + n_dec + 2) / 4.0 + 1.0 / 128.0
     return 40.0 * blocks + 2.0 * m + n_dec + 2.0 + 12.0 + 8.0, blocks
 
 
-def paper_leg(pcpd, mcs: int = 200, systems: int = 4096):
+def paper_leg(pcpd, mcs: int = 1000, systems: int = 3648):
     """The paper's own scheme (Sec. 3-4, Alg. 2) at the layout it reports: rings of
     L = 65536 sites (S_w = 64 threads x n_loc = 32 words, and S_w = 32 x 64), d = 1/2
-    (m = 1 plane), n_dec = 2 decorrelation words, p = 0.15, full start, `systems` systems,
-    20 log-spaced records; `mcs` MCS timed after 1 MCS of warm-up."""
+    (m = 1 plane), n_dec = 2 decorrelation words, p = 0.15, full start, `systems` systems
+    (3648 = 152 SMs x 24 resident systems: one full wave), 20 log-spaced records; `mcs` MCS
+    timed after 1 MCS of warm-up."""
     import torch
     out = []
     m, n_dec = 1, 2

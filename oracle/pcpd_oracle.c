@@ -431,35 +431,48 @@ void orc_unpack(const uint32_t *words, uint32_t L, uint32_t S, uint8_t *state)
  * word i holds site b*(L/32) + w*n_loc + i ("connected lattices", Sec. 4).  Every step
  * draws one local site i* for the whole system and every workitem updates, for all 32 bits
  * at once, the bond (s, s+1) with s = b*(L/32) + w*n_loc + i*, fission going to s-1 or s+2
- * (all mod L).  Per workitem and step the random words, in stream order, are: m planes of
- * the diffusion draw (bit b diffuses iff its m-bit value, MSB first, is below T_d =
- * d*2^m), n_dec decorrelation words (ANDed), one word compared with T_c =
- * floor(p*2^n_dec*2^32) and broadcast to all bits (the correlated annihilation draw), one
- * fission-direction word (bit 1: high, s+2).  A bit annihilates iff no diffusion, an
- * occupied pair, all decorrelation bits 1 and the broadcast draw true.  One step = 32*S_w
- * attempts; MCS time t is step t*n_loc.
- * Random words: block j of Philox counter (w, step, system, TAG_PAPER<<28 | j), words
- * taken in order; the local site: floor(x0 * n_loc / 2^32) of (0, step, system,
+ * (all mod L).  Each RNG() of Alg. 2 returns the next word of the workitem's own random
+ * stream; a step takes n_w = m + n_dec + 2 words in this order: m planes of the diffusion
+ * draw (bit b diffuses iff its m-bit value, MSB first, is below T_d = d*2^m), n_dec
+ * decorrelation words (ANDed), one word compared with T_c = floor(p*2^n_dec*2^32) and
+ * broadcast to all bits (the correlated annihilation draw), one fission-direction word (bit
+ * 1: high, s+2).  A bit annihilates iff no diffusion, an occupied pair, all decorrelation
+ * bits 1 and the broadcast draw true.  One step = 32*S_w attempts; MCS time t is step
+ * t*n_loc.
+ * Random streams (Philox4x32-10 keyed by the seed): word k of workitem w's stream in system
+ * sys is word k mod 4 of the block counted by (w, B mod 2^32, sys, TAG_PAPER<<28 | B>>32),
+ * B = floor(k/4); step t takes words n_w*t .. n_w*t + n_w - 1.  The local site of step t is
+ * floor(x * n_loc / 2^32), x = word t mod 4 of the block (0, floor(t/4), sys,
  * TAG_PAPER_SITE<<28).  state: bytes [systems][L] of systems sys0, sys0+1, ...;
  * rec_sys (nullable): per-system counts [n_rec][systems].
  * ------------------------------------------------------------------------------------- */
 #define ORC_TAG_PAPER 4u
 #define ORC_TAG_PAPER_SITE 5u
 
+/* Word k of workitem w's stream in system sys. */
+static uint32_t orc_paper_word(uint64_t seed, uint32_t w, uint32_t sys, uint64_t k)
+{
+    uint32_t x[4];
+    const uint64_t B = k / 4u;
+    orc_block(seed, w, (uint32_t)B, sys, (ORC_TAG_PAPER << 28) | (uint32_t)(B >> 32), x);
+    return x[k % 4u];
+}
+
 int orc_paper_run(uint32_t n_loc, uint32_t S_w, uint32_t systems, uint32_t m, uint32_t t_d,
                   uint32_t n_dec, uint64_t t_c, uint64_t seed, uint8_t *state, uint64_t step_begin,
                   uint64_t step_end, const uint64_t *rec_step, uint32_t n_rec, uint64_t *rec_total,
                   uint32_t sys0, uint32_t *rec_sys)
 {
-    if (n_loc < 4 || S_w == 0 || m > 16 || (t_d >> m) > 1 || (t_d > (1u << m)) || n_dec > 16 ||
+    if (n_loc < 4 || S_w == 0 || m > 16 || (t_d > (1u << m)) || n_dec > 16 ||
         step_end > 0xFFFFFFFFull || step_end < step_begin)
         return 1;
     const uint64_t L = 32ull * n_loc * S_w;
     const uint32_t nw = m + n_dec + 2;   /* words per workitem and step */
     for (uint32_t r = 0; r < n_rec; ++r) rec_total[r] = 0;
-    uint32_t *words = (uint32_t *)calloc((size_t)nw + 4, sizeof(uint32_t));
+    uint32_t words[36];
     for (uint32_t sys = 0; sys < systems; ++sys) {
         uint8_t *q = state + (uint64_t)sys * L;
+        const uint32_t gsys = sys0 + sys;
         uint32_t r = 0;
         while (r < n_rec && rec_step[r] < step_begin) ++r;
         for (uint64_t st = step_begin;; ++st) {
@@ -472,11 +485,11 @@ int orc_paper_run(uint32_t n_loc, uint32_t S_w, uint32_t systems, uint32_t m, ui
             }
             if (st == step_end) break;
             uint32_t xs[4];
-            orc_block(seed, 0u, (uint32_t)st, sys0 + sys, ORC_TAG_PAPER_SITE << 28, xs);
-            const uint32_t istar = (uint32_t)(((uint64_t)xs[0] * n_loc) >> 32);
+            orc_block(seed, 0u, (uint32_t)(st / 4u), gsys, ORC_TAG_PAPER_SITE << 28, xs);
+            const uint32_t istar = (uint32_t)(((uint64_t)xs[st % 4u] * n_loc) >> 32);
             for (uint32_t w = 0; w < S_w; ++w) {
-                for (uint32_t j = 0; 4 * j < nw; ++j)
-                    orc_block(seed, w, (uint32_t)st, sys0 + sys, (ORC_TAG_PAPER << 28) | j, words + 4 * j);
+                for (uint32_t i = 0; i < nw; ++i)
+                    words[i] = orc_paper_word(seed, w, gsys, (uint64_t)nw * st + i);
                 const uint32_t corr = ((uint64_t)words[m + n_dec] < t_c) ? 1u : 0u;
                 const uint32_t fis = words[m + n_dec + 1];
                 for (uint32_t b = 0; b < 32; ++b) {
@@ -505,6 +518,5 @@ int orc_paper_run(uint32_t n_loc, uint32_t S_w, uint32_t systems, uint32_t m, ui
             }
         }
     }
-    free(words);
     return 0;
 }

@@ -1868,26 +1868,28 @@ namespace {
 
 using PaperKernel = void (*)(const pcpdk::PaperParams);
 
-// Compile-time plane/decorrelation counts for the common cases, a generic kernel otherwise.
+// Compile-time plane/decorrelation counts for the common cases and CTAs of up to 256
+// threads; a kernel that reads them at run time otherwise.
 template <int M>
 PaperKernel paper_kernel_m(uint32_t nd) {
   switch (nd) {
-    case 0: return pcpdk::k_paper_sweep<M, 0>;
-    case 1: return pcpdk::k_paper_sweep<M, 1>;
-    case 2: return pcpdk::k_paper_sweep<M, 2>;
-    case 3: return pcpdk::k_paper_sweep<M, 3>;
-    default: return pcpdk::k_paper_sweep<-1, 0>;
+    case 0: return pcpdk::k_paper_sweep<M, 0, 256>;
+    case 1: return pcpdk::k_paper_sweep<M, 1, 256>;
+    case 2: return pcpdk::k_paper_sweep<M, 2, 256>;
+    case 3: return pcpdk::k_paper_sweep<M, 3, 256>;
+    default: return pcpdk::k_paper_sweep<-1, 0, 256>;
   }
 }
 
-PaperKernel paper_kernel(uint32_t m, uint32_t nd, int generic) {
-  if (generic) return pcpdk::k_paper_sweep<-1, 0>;
+PaperKernel paper_kernel(uint32_t m, uint32_t nd, uint32_t threads, int generic) {
+  if (threads > 256) return pcpdk::k_paper_sweep<-1, 0, 1024>;
+  if (generic) return pcpdk::k_paper_sweep<-1, 0, 256>;
   switch (m) {
     case 0: return paper_kernel_m<0>(nd);
     case 1: return paper_kernel_m<1>(nd);
     case 2: return paper_kernel_m<2>(nd);
     case 3: return paper_kernel_m<3>(nd);
-    default: return pcpdk::k_paper_sweep<-1, 0>;
+    default: return pcpdk::k_paper_sweep<-1, 0, 256>;
   }
 }
 
@@ -2002,7 +2004,7 @@ int pcpd_paper_create(const pcpd_paper_params *prm, pcpd_paper_t **out) {
   h->threads = spc * h->S_w;
   h->grid = (h->systems + spc - 1) / spc;
   h->smem = (size_t)spc * words * 4;
-  h->kernel = paper_kernel(h->m, h->n_dec, prm->generic);
+  h->kernel = paper_kernel(h->m, h->n_dec, h->threads, prm->generic);
   rc = paper_smem_optin(h->kernel, h->smem);
   if (rc) return bail(rc);
   if (prm->stream) {

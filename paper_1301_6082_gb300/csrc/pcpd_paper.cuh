@@ -11,19 +11,26 @@
 // previous thread's column; past the system's last (first) column they are the next (previous)
 // bit of column 0 (S_w - 1), which is a one-bit rotation of that word.
 //
-// Random words per thread and step, in stream order: m diffusion planes (a bit diffuses iff
-// its m-bit value, most significant plane first, is below T_d = d * 2^m: the dyadic masks of
+// Each RNG() of Alg. 2 returns the next word of the thread's own random stream.  A step
+// takes n_w = m + n_dec + 2 words, in this order: m diffusion planes (a bit diffuses iff its
+// m-bit value, most significant plane first, is below T_d = d * 2^m: the dyadic masks of
 // Sec. 4.2), n_dec decorrelation words ANDed together (Sec. 4.3), one word compared with
 // T_c = floor(p * 2^n_dec * 2^32) whose outcome is broadcast to all 32 bits (the correlated
-// annihilation draw of Sec. 4.3), and one fission-direction word (bit 1: to s+2).  They are
-// Philox4x32-10 blocks j = 0, 1, ... of the counter (w, step, system, TAG_PAPER<<28 | j);
-// the local site is floor(x0 * n_loc / 2^32) of (0, step, system, TAG_PAPER_SITE<<28).
+// annihilation draw of Sec. 4.3), and one fission-direction word (bit 1: to s+2).  Word k of
+// the stream of thread w in system sys is word k mod 4 of the Philox4x32-10 block counted by
+// (w, B mod 2^32, sys, TAG_PAPER<<28 | B>>32), B = floor(k/4); step t takes words n_w*t ..
+// n_w*t + n_w - 1, so four consecutive steps starting at a multiple of 4 use exactly n_w
+// whole blocks.  The local site of step t is floor(x * n_loc / 2^32), x = word t mod 4 of the
+// block (0, floor(t/4), sys, TAG_PAPER_SITE<<28).
 //
 // GB300 layout: the system's n_loc * S_w words stay in shared memory for the whole launch,
 // word (l, w) at l * S_w + w, so a step's four loads and stores per thread are consecutive
 // across the warp (bank-conflict free, the shared-memory analogue of the paper's coalesced
-// 4*S_w-byte rows).  Between steps the S_w threads of a system meet at a named barrier (one
-// warp: __syncwarp), so systems in one CTA run independently.
+// 4*S_w-byte rows).  A thread touches another thread's column only in a step whose local
+// site is within one word of a column end (l* = 0, n_loc-2 or n_loc-1); the S_w threads of a
+// system meet at a named barrier (one warp: __syncwarp) just before and just after such a
+// step and nowhere else, so systems in one CTA run independently and most steps run without
+// a barrier.
 #pragma once
 #include "pcpd_kernels.cuh"
 
@@ -54,47 +61,64 @@ __device__ __forceinline__ void paper_barrier(uint32_t id, uint32_t nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
-// Per-thread masks of one step: D (diffuse), A (annihilate if the bond is an occupied pair and
-// D is clear: decorrelation AND broadcast draw), F (fission direction, 1 = high).
-// M, ND >= 0: plane and decorrelation counts fixed at compile time; M < 0: read from P.
-template <int M, int ND>
-__device__ __forceinline__ void paper_masks(const PaperParams &P, uint32_t w, uint32_t st,
-                                            uint32_t sys, uint32_t &D, uint32_t &A,
-                                            uint32_t &F) {
-  const uint32_t m = M >= 0 ? (uint32_t)M : P.m;
-  const uint32_t nd = M >= 0 ? (uint32_t)ND : P.n_dec;
-  const uint32_t nw = m + nd + 2u;
-  uint32_t lt = 0u, eq = ~0u, dec = ~0u, corr = 0u, fis = 0u;
-#pragma unroll
-  for (uint32_t j = 0; 4u * j < nw; ++j) {
-    uint32_t x0 = w, x1 = st, x2 = sys, x3 = (kTagPaper << 28) | j;
-    philox4x32_10_rk(x0, x1, x2, x3, P.rk);
-    const uint32_t xs[4] = {x0, x1, x2, x3};
-#pragma unroll
-    for (uint32_t q = 0; q < 4u; ++q) {
-      const int k = (int)(4u * j + q), im = (int)m, ind = (int)nd;
-      const uint32_t u = xs[q];
-      if (k < im) {
-        // plane k carries bit (m-1-k) of each lane's draw; compare with T_d, MSB first
-        const uint32_t tb = 0u - ((P.t_d >> (im - 1 - k)) & 1u);
-        lt |= eq & ~u & tb;
-        eq &= ~(u ^ tb);
-      } else if (k < im + ind) {
-        dec &= u;
-      } else if (k == im + ind) {
-        corr = (P.tc_full || u < P.tc) ? ~0u : 0u;
-      } else if (k == im + ind + 1) {
-        fis = u;
-      }
-    }
-  }
-  D = P.d_full ? ~0u : lt;
-  A = dec & corr;
-  F = fis;
+__device__ __forceinline__ uint32_t pick4(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                          uint32_t i) {
+  return i == 0u ? c0 : i == 1u ? c1 : i == 2u ? c2 : c3;
 }
 
-template <int M, int ND>
-__global__ void __launch_bounds__(1024) k_paper_sweep(const PaperParams P) {
+// Occupied sites of the thread's column, summed over the system, added to record slot r.
+__device__ __forceinline__ void paper_record(const PaperParams &P, const uint32_t *lat,
+                                             uint32_t w, uint32_t sys, uint32_t r) {
+  uint32_t c = 0u;
+  for (uint32_t l = 0; l < P.n_loc; ++l) c += __popc(lat[l * P.S_w + w]);
+  c = __reduce_add_sync(~0u, c);
+  if ((threadIdx.x & 31u) == 0u) {
+    atomicAdd(P.rec_total + r, (unsigned long long)c);
+    if (P.rec_sys) atomicAdd(P.rec_sys + (size_t)r * P.systems_total + sys, c);
+  }
+}
+
+// One step of Alg. 2 for thread w at local site ls, given its masks D, A, F.
+__device__ __forceinline__ void paper_step(uint32_t *lat, uint32_t n_loc, uint32_t S_w,
+                                           uint32_t w, uint32_t w_lo, uint32_t rot_lo,
+                                           uint32_t w_hi, uint32_t rot_hi, uint32_t ls,
+                                           uint32_t D, uint32_t A, uint32_t F) {
+  // word indexes and seam rotations of sites s-1, s, s+1, s+2
+  const uint32_t i_a = (ls == 0u) ? (n_loc - 1u) * S_w + w_lo : (ls - 1u) * S_w + w;
+  const uint32_t r_a = (ls == 0u) ? rot_lo : 0u;
+  const uint32_t i_0 = ls * S_w + w;
+  const uint32_t i_1 = (ls + 1u < n_loc) ? (ls + 1u) * S_w + w : w_hi;
+  const uint32_t r_1 = (ls + 1u < n_loc) ? 0u : rot_hi;
+  const uint32_t i_2 = (ls + 2u < n_loc) ? (ls + 2u) * S_w + w : (ls + 2u - n_loc) * S_w + w_hi;
+  const uint32_t r_2 = (ls + 2u < n_loc) ? 0u : rot_hi;
+  // in the thread's frame bit b of every value is the site of bit b's segment
+  uint32_t a = __funnelshift_l(lat[i_a], lat[i_a], r_a);
+  uint32_t b0 = lat[i_0];
+  uint32_t b1 = __funnelshift_r(lat[i_1], lat[i_1], r_1);
+  uint32_t c2 = __funnelshift_r(lat[i_2], lat[i_2], r_2);
+  // swap under D; else an occupied pair annihilates under A, else fissions to s+2 (F = 1)
+  // or to s-1 (F = 0)
+  const uint32_t pair = b0 & b1;
+  const uint32_t n0 = (D & b1) | (~D & b0);
+  const uint32_t n1 = (D & b0) | (~D & b1);
+  const uint32_t react = ~D & pair;
+  const uint32_t ann = react & A;
+  const uint32_t fis = react & ~ann;
+  b0 = n0 & ~ann;
+  b1 = n1 & ~ann;
+  c2 |= fis & F;
+  a |= fis & ~F;
+  lat[i_a] = __funnelshift_r(a, a, r_a);
+  lat[i_0] = b0;
+  lat[i_1] = __funnelshift_l(b1, b1, r_1);
+  lat[i_2] = __funnelshift_l(c2, c2, r_2);
+}
+
+// M, ND >= 0: plane and decorrelation counts fixed at compile time (every word position in
+// a 4-step group is then a constant); M < 0: read from P.  MAXT: largest CTA the kernel
+// serves; CTAs of up to 256 threads get a register budget that keeps 6 of them per SM.
+template <int M, int ND, int MAXT>
+__global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 6 : 1) k_paper_sweep(const PaperParams P) {
   extern __shared__ uint32_t s_lat[];
   const uint32_t S_w = P.S_w, n_loc = P.n_loc;
   const uint32_t slot = threadIdx.x / S_w, w = threadIdx.x - slot * S_w;
@@ -104,73 +128,70 @@ __global__ void __launch_bounds__(1024) k_paper_sweep(const PaperParams P) {
   const uint32_t words = n_loc * S_w;
   uint32_t *lat = s_lat + (size_t)slot * words;
   uint32_t *glat = P.lat + (size_t)sys * words;
+  // thread w loads, updates (outside the barrier-guarded steps) and stores only column w
   for (uint32_t i = w; i < words; i += S_w) lat[i] = __ldcg(glat + i);
-  paper_barrier(bar, S_w);
 
+  const uint32_t m = M >= 0 ? (uint32_t)M : P.m;
+  const uint32_t nd = M >= 0 ? (uint32_t)ND : P.n_dec;
+  const uint32_t nw = m + nd + 2u;
   const uint32_t lane = threadIdx.x & 31u;
-  // neighbour columns and the bit rotation at the system's seam
   const uint32_t w_lo = (w == 0u) ? S_w - 1u : w - 1u, rot_lo = (w == 0u) ? 1u : 0u;
   const uint32_t w_hi = (w == S_w - 1u) ? 0u : w + 1u, rot_hi = (w == S_w - 1u) ? 1u : 0u;
-  uint32_t site_cache = 0u;
+  const uint32_t begin = P.step_begin, end = P.step_end;
   uint32_t r = 0u;
-  for (uint32_t st = P.step_begin;; ++st) {
-    if (r < P.n_rec && P.rec_step[r] == (unsigned long long)st) {
-      uint32_t c = 0u;
-      for (uint32_t l = 0; l < n_loc; ++l) c += __popc(lat[l * S_w + w]);
-      c = __reduce_add_sync(~0u, c);
-      if (lane == 0u) {
-        atomicAdd(P.rec_total + r, (unsigned long long)c);
-        if (P.rec_sys) atomicAdd(P.rec_sys + (size_t)r * P.systems_total + sys, c);
+  if (begin < end) {
+    const uint32_t q0 = begin >> 2, q1 = (end - 1u) >> 2;
+    uint32_t s0 = 0u, s1 = 0u, s2 = 0u, s3 = 0u;  // local-site words of this lane's group
+    for (uint32_t q = q0; q <= q1; ++q) {
+      const uint32_t qi = (q - q0) & 31u;
+      if (qi == 0u) {
+        // lane i draws the local sites of the 4 steps of group q + i
+        uint32_t x0 = 0u, x1 = q + lane, x2 = sys, x3 = kTagPaperSite << 28;
+        philox4x32_10_rk(x0, x1, x2, x3, P.rk);
+        s0 = x0, s1 = x1, s2 = x2, s3 = x3;
       }
-      ++r;
-      paper_barrier(bar, S_w);  // counting reads neighbour-written words of the next step
+      const unsigned long long B0 = (unsigned long long)q * nw;  // first block of the group
+      uint32_t c0 = 0u, c1 = 0u, c2 = 0u, c3 = 0u;
+#pragma unroll
+      for (uint32_t j = 0; j < 4u; ++j) {
+        const uint32_t st = 4u * q + j;
+        uint32_t lt = 0u, eq = ~0u, dec = ~0u, corr = 0u, fis = 0u;
+#pragma unroll
+        for (uint32_t i = 0; i < nw; ++i) {
+          const uint32_t k = j * nw + i;
+          if ((k & 3u) == 0u) {
+            const unsigned long long B = B0 + (k >> 2);
+            uint32_t x0 = w, x1 = (uint32_t)B, x2 = sys, x3 = (kTagPaper << 28) | (uint32_t)(B >> 32);
+            philox4x32_10_rk(x0, x1, x2, x3, P.rk);
+            c0 = x0, c1 = x1, c2 = x2, c3 = x3;
+          }
+          const uint32_t u = pick4(c0, c1, c2, c3, k & 3u);
+          if ((int)i < (int)m) {
+            // plane i carries bit (m-1-i) of each lane's draw; compare with T_d, MSB first
+            const uint32_t tb = 0u - ((P.t_d >> (m - 1u - i)) & 1u);
+            lt |= eq & ~u & tb;
+            eq &= ~(u ^ tb);
+          } else if ((int)i < (int)(m + nd)) {
+            dec &= u;
+          } else if (i == m + nd) {
+            corr = (P.tc_full || u < P.tc) ? ~0u : 0u;
+          } else {
+            fis = u;
+          }
+        }
+        if (st < begin || st >= end) continue;  // a partial group at a launch edge
+        if (r < P.n_rec && P.rec_step[r] == (unsigned long long)st) paper_record(P, lat, w, sys, r++);
+        const uint32_t x = __shfl_sync(~0u, pick4(s0, s1, s2, s3, j), qi);
+        const uint32_t ls = (uint32_t)(((unsigned long long)x * n_loc) >> 32);
+        const bool cross = ls == 0u || ls + 2u >= n_loc;
+        if (cross) paper_barrier(bar, S_w);
+        paper_step(lat, n_loc, S_w, w, w_lo, rot_lo, w_hi, rot_hi, ls, P.d_full ? ~0u : lt,
+                   dec & corr, fis);
+        if (cross) paper_barrier(bar, S_w);
+      }
     }
-    if (st == P.step_end) break;
-    const uint32_t q = (st - P.step_begin) & 31u;
-    if (q == 0u) {
-      // lane i draws the local site of step st + i; the warp reads them one per step
-      uint32_t x0 = 0u, x1 = st + lane, x2 = sys, x3 = kTagPaperSite << 28;
-      philox4x32_10_rk(x0, x1, x2, x3, P.rk);
-      site_cache = (uint32_t)(((unsigned long long)x0 * n_loc) >> 32);
-    }
-    const uint32_t ls = __shfl_sync(~0u, site_cache, q);
-
-    uint32_t D, A, F;
-    paper_masks<M, ND>(P, w, st, sys, D, A, F);
-
-    // word indexes and seam rotations of sites s-1, s, s+1, s+2
-    const uint32_t i_a = (ls == 0u) ? (n_loc - 1u) * S_w + w_lo : (ls - 1u) * S_w + w;
-    const uint32_t r_a = (ls == 0u) ? rot_lo : 0u;
-    const uint32_t i_0 = ls * S_w + w;
-    const uint32_t i_1 = (ls + 1u < n_loc) ? (ls + 1u) * S_w + w : w_hi;
-    const uint32_t r_1 = (ls + 1u < n_loc) ? 0u : rot_hi;
-    const uint32_t i_2 = (ls + 2u < n_loc) ? (ls + 2u) * S_w + w : (ls + 2u - n_loc) * S_w + w_hi;
-    const uint32_t r_2 = (ls + 2u < n_loc) ? 0u : rot_hi;
-    // in the thread's frame bit b of every value is the site of bit b's segment
-    uint32_t a = __funnelshift_l(lat[i_a], lat[i_a], r_a);
-    uint32_t b0 = lat[i_0];
-    uint32_t b1 = __funnelshift_r(lat[i_1], lat[i_1], r_1);
-    uint32_t c2 = __funnelshift_r(lat[i_2], lat[i_2], r_2);
-
-    // Alg. 2 as bit logic: swap under D; else an occupied pair annihilates under A, else
-    // fissions to s+2 (F = 1) or s-1 (F = 0).
-    const uint32_t pair = b0 & b1;
-    const uint32_t n0 = (D & b1) | (~D & b0);
-    const uint32_t n1 = (D & b0) | (~D & b1);
-    const uint32_t react = ~D & pair;
-    const uint32_t ann = react & A;
-    const uint32_t fis = react & ~ann;
-    b0 = n0 & ~ann;
-    b1 = n1 & ~ann;
-    c2 |= fis & F;
-    a |= fis & ~F;
-
-    lat[i_a] = __funnelshift_r(a, a, r_a);
-    lat[i_0] = b0;
-    lat[i_1] = __funnelshift_l(b1, b1, r_1);
-    lat[i_2] = __funnelshift_l(c2, c2, r_2);
-    paper_barrier(bar, S_w);
   }
+  if (r < P.n_rec && P.rec_step[r] == (unsigned long long)end) paper_record(P, lat, w, sys, r++);
   for (uint32_t i = w; i < words; i += S_w) __stcg(glat + i, lat[i]);
 }
 
