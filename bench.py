@@ -356,6 +356,9 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-stream", action="store_true")
     ap.add_argument("--no-paper", action="store_true")
+    ap.add_argument("--paper-only", action="store_true",
+                    help="run only the paper-scheme leg (for profiling) and print its JSON")
+    ap.add_argument("--paper-mcs", type=int, default=1000)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -370,6 +373,9 @@ def main():
     from paper_1301_6082_gb300 import pcpd
 
     torch.cuda.set_device(local)
+    if args.paper_only:
+        print(json.dumps({"paper_scheme": paper_leg(pcpd, mcs=args.paper_mcs)}), flush=True)
+        return 0
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -490,7 +496,7 @@ def main():
     batch = batch_leg(pcpd) if not args.no_batch else None
     serving = serving_leg(pcpd) if not args.no_serve else None
     streamed = stream_leg(pcpd) if not args.no_stream else None
-    paper = paper_leg(pcpd) if not args.no_paper else None
+    paper = paper_leg(pcpd, mcs=args.paper_mcs) if not args.no_paper else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

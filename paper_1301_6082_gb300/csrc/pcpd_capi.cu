@@ -1904,6 +1904,9 @@ int paper_smem_optin(PaperKernel k, size_t bytes) {
   int rc = smem_optin(&optin);
   if (rc) return rc;
   CU(cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  // all of the SM's unified L1/shared storage as shared memory: the systems are the working set
+  CU(cudaFuncSetAttribute((const void *)k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                          (int)cudaSharedmemCarveoutMaxShared));
   done.emplace_back((const void *)k, (size_t)optin);
   return PCPD_OK;
 }

@@ -78,26 +78,11 @@ __device__ __forceinline__ void paper_record(const PaperParams &P, const uint32_
   }
 }
 
-// One step of Alg. 2 for thread w at local site ls, given its masks D, A, F.
-__device__ __forceinline__ void paper_step(uint32_t *lat, uint32_t n_loc, uint32_t S_w,
-                                           uint32_t w, uint32_t w_lo, uint32_t rot_lo,
-                                           uint32_t w_hi, uint32_t rot_hi, uint32_t ls,
-                                           uint32_t D, uint32_t A, uint32_t F) {
-  // word indexes and seam rotations of sites s-1, s, s+1, s+2
-  const uint32_t i_a = (ls == 0u) ? (n_loc - 1u) * S_w + w_lo : (ls - 1u) * S_w + w;
-  const uint32_t r_a = (ls == 0u) ? rot_lo : 0u;
-  const uint32_t i_0 = ls * S_w + w;
-  const uint32_t i_1 = (ls + 1u < n_loc) ? (ls + 1u) * S_w + w : w_hi;
-  const uint32_t r_1 = (ls + 1u < n_loc) ? 0u : rot_hi;
-  const uint32_t i_2 = (ls + 2u < n_loc) ? (ls + 2u) * S_w + w : (ls + 2u - n_loc) * S_w + w_hi;
-  const uint32_t r_2 = (ls + 2u < n_loc) ? 0u : rot_hi;
-  // in the thread's frame bit b of every value is the site of bit b's segment
-  uint32_t a = __funnelshift_l(lat[i_a], lat[i_a], r_a);
-  uint32_t b0 = lat[i_0];
-  uint32_t b1 = __funnelshift_r(lat[i_1], lat[i_1], r_1);
-  uint32_t c2 = __funnelshift_r(lat[i_2], lat[i_2], r_2);
-  // swap under D; else an occupied pair annihilates under A, else fissions to s+2 (F = 1)
-  // or to s-1 (F = 0)
+// Alg. 2 on one bond as bit logic, in the thread's frame (bit b of every value is a site of
+// bit b's segment): swap (b0, b1) under D; else an occupied pair annihilates under A, else
+// puts a particle on c2 = s+2 (F = 1) or on a = s-1 (F = 0).
+__device__ __forceinline__ void paper_bond(uint32_t &a, uint32_t &b0, uint32_t &b1,
+                                           uint32_t &c2, uint32_t D, uint32_t A, uint32_t F) {
   const uint32_t pair = b0 & b1;
   const uint32_t n0 = (D & b1) | (~D & b0);
   const uint32_t n1 = (D & b0) | (~D & b1);
@@ -108,11 +93,36 @@ __device__ __forceinline__ void paper_step(uint32_t *lat, uint32_t n_loc, uint32
   b1 = n1 & ~ann;
   c2 |= fis & F;
   a |= fis & ~F;
+}
+
+// A step whose four sites reach into a neighbouring column (l* = 0, n_loc-2 or n_loc-1):
+// word indexes with the wrap to the next/previous thread and the bit rotation at the seam.
+__device__ __forceinline__ void paper_step_cross(uint32_t *lat, uint32_t n_loc, uint32_t S_w,
+                                                 uint32_t w, uint32_t w_lo, uint32_t rot_lo,
+                                                 uint32_t w_hi, uint32_t rot_hi, uint32_t ls,
+                                                 uint32_t D, uint32_t A, uint32_t F) {
+  const uint32_t i_a = (ls == 0u) ? (n_loc - 1u) * S_w + w_lo : (ls - 1u) * S_w + w;
+  const uint32_t r_a = (ls == 0u) ? rot_lo : 0u;
+  const uint32_t i_0 = ls * S_w + w;
+  const uint32_t i_1 = (ls + 1u < n_loc) ? (ls + 1u) * S_w + w : w_hi;
+  const uint32_t r_1 = (ls + 1u < n_loc) ? 0u : rot_hi;
+  const uint32_t i_2 = (ls + 2u < n_loc) ? (ls + 2u) * S_w + w : (ls + 2u - n_loc) * S_w + w_hi;
+  const uint32_t r_2 = (ls + 2u < n_loc) ? 0u : rot_hi;
+  uint32_t a = __funnelshift_l(lat[i_a], lat[i_a], r_a);
+  uint32_t b0 = lat[i_0];
+  uint32_t b1 = __funnelshift_r(lat[i_1], lat[i_1], r_1);
+  uint32_t c2 = __funnelshift_r(lat[i_2], lat[i_2], r_2);
+  paper_bond(a, b0, b1, c2, D, A, F);
   lat[i_a] = __funnelshift_r(a, a, r_a);
   lat[i_0] = b0;
   lat[i_1] = __funnelshift_l(b1, b1, r_1);
   lat[i_2] = __funnelshift_l(c2, c2, r_2);
 }
+
+template <bool B>
+struct PaperEdge {
+  static constexpr bool value = B;
+};
 
 // M, ND >= 0: plane and decorrelation counts fixed at compile time (every word position in
 // a 4-step group is then a constant); M < 0: read from P.  MAXT: largest CTA the kernel
@@ -138,60 +148,87 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 6 : 1) k_paper_sweep(const
   const uint32_t w_lo = (w == 0u) ? S_w - 1u : w - 1u, rot_lo = (w == 0u) ? 1u : 0u;
   const uint32_t w_hi = (w == S_w - 1u) ? 0u : w + 1u, rot_hi = (w == S_w - 1u) ? 1u : 0u;
   const uint32_t begin = P.step_begin, end = P.step_end;
+  // record slots: r, and the step of the next one (steps inside the loop are < 2^32 - 1)
   uint32_t r = 0u;
-  if (begin < end) {
-    const uint32_t q0 = begin >> 2, q1 = (end - 1u) >> 2;
-    uint32_t s0 = 0u, s1 = 0u, s2 = 0u, s3 = 0u;  // local-site words of this lane's group
-    for (uint32_t q = q0; q <= q1; ++q) {
-      const uint32_t qi = (q - q0) & 31u;
-      if (qi == 0u) {
-        // lane i draws the local sites of the 4 steps of group q + i
-        uint32_t x0 = 0u, x1 = q + lane, x2 = sys, x3 = kTagPaperSite << 28;
-        philox4x32_10_rk(x0, x1, x2, x3, P.rk);
-        s0 = x0, s1 = x1, s2 = x2, s3 = x3;
-      }
-      const unsigned long long B0 = (unsigned long long)q * nw;  // first block of the group
-      uint32_t c0 = 0u, c1 = 0u, c2 = 0u, c3 = 0u;
+  uint32_t next_rec = P.n_rec ? (uint32_t)P.rec_step[0] : 0xFFFFFFFFu;
+  uint32_t s0 = 0u, s1 = 0u, s2 = 0u, s3 = 0u;  // local-site words of this lane's group
+  uint32_t q0 = begin >> 2;
+
+  // one group of 4 steps (4q .. 4q+3); EDGE: the group may extend past [begin, end)
+  auto group = [&](uint32_t q, auto edge) {
+    constexpr bool EDGE = decltype(edge)::value;
+    const uint32_t qi = (q - q0) & 31u;
+    if (qi == 0u) {
+      // lane i draws the local sites of the 4 steps of group q + i
+      uint32_t x0 = 0u, x1 = q + lane, x2 = sys, x3 = kTagPaperSite << 28;
+      philox4x32_10_rk(x0, x1, x2, x3, P.rk);
+      s0 = x0, s1 = x1, s2 = x2, s3 = x3;
+    }
+    const unsigned long long B0 = (unsigned long long)q * nw;  // first block of the group
+    uint32_t c0 = 0u, c1 = 0u, c2 = 0u, c3 = 0u;
 #pragma unroll
-      for (uint32_t j = 0; j < 4u; ++j) {
-        const uint32_t st = 4u * q + j;
-        uint32_t lt = 0u, eq = ~0u, dec = ~0u, corr = 0u, fis = 0u;
+    for (uint32_t j = 0; j < 4u; ++j) {
+      const uint32_t st = 4u * q + j;
+      uint32_t lt = 0u, eq = ~0u, dec = ~0u, corr = 0u, fis = 0u;
 #pragma unroll
-        for (uint32_t i = 0; i < nw; ++i) {
-          const uint32_t k = j * nw + i;
-          if ((k & 3u) == 0u) {
-            const unsigned long long B = B0 + (k >> 2);
-            uint32_t x0 = w, x1 = (uint32_t)B, x2 = sys, x3 = (kTagPaper << 28) | (uint32_t)(B >> 32);
-            philox4x32_10_rk(x0, x1, x2, x3, P.rk);
-            c0 = x0, c1 = x1, c2 = x2, c3 = x3;
-          }
-          const uint32_t u = pick4(c0, c1, c2, c3, k & 3u);
-          if ((int)i < (int)m) {
-            // plane i carries bit (m-1-i) of each lane's draw; compare with T_d, MSB first
-            const uint32_t tb = 0u - ((P.t_d >> (m - 1u - i)) & 1u);
-            lt |= eq & ~u & tb;
-            eq &= ~(u ^ tb);
-          } else if ((int)i < (int)(m + nd)) {
-            dec &= u;
-          } else if (i == m + nd) {
-            corr = (P.tc_full || u < P.tc) ? ~0u : 0u;
-          } else {
-            fis = u;
-          }
+      for (uint32_t i = 0; i < nw; ++i) {
+        const uint32_t k = j * nw + i;
+        if ((k & 3u) == 0u) {
+          const unsigned long long B = B0 + (k >> 2);
+          uint32_t x0 = w, x1 = (uint32_t)B, x2 = sys, x3 = (kTagPaper << 28) | (uint32_t)(B >> 32);
+          philox4x32_10_rk(x0, x1, x2, x3, P.rk);
+          c0 = x0, c1 = x1, c2 = x2, c3 = x3;
         }
-        if (st < begin || st >= end) continue;  // a partial group at a launch edge
-        if (r < P.n_rec && P.rec_step[r] == (unsigned long long)st) paper_record(P, lat, w, sys, r++);
-        const uint32_t x = __shfl_sync(~0u, pick4(s0, s1, s2, s3, j), qi);
-        const uint32_t ls = (uint32_t)(((unsigned long long)x * n_loc) >> 32);
-        const bool cross = ls == 0u || ls + 2u >= n_loc;
-        if (cross) paper_barrier(bar, S_w);
-        paper_step(lat, n_loc, S_w, w, w_lo, rot_lo, w_hi, rot_hi, ls, P.d_full ? ~0u : lt,
-                   dec & corr, fis);
-        if (cross) paper_barrier(bar, S_w);
+        const uint32_t u = pick4(c0, c1, c2, c3, k & 3u);
+        if ((int)i < (int)m) {
+          // plane i carries bit (m-1-i) of each lane's draw; compare with T_d, MSB first
+          const uint32_t tb = 0u - ((P.t_d >> (m - 1u - i)) & 1u);
+          lt |= eq & ~u & tb;
+          eq &= ~(u ^ tb);
+        } else if ((int)i < (int)(m + nd)) {
+          dec &= u;
+        } else if (i == m + nd) {
+          corr = (P.tc_full || u < P.tc) ? ~0u : 0u;
+        } else {
+          fis = u;
+        }
+      }
+      if (EDGE && (st < begin || st >= end)) continue;
+      if (st == next_rec) {
+        paper_record(P, lat, w, sys, r);
+        ++r;
+        next_rec = r < P.n_rec ? (uint32_t)P.rec_step[r] : 0xFFFFFFFFu;
+      }
+      const uint32_t x = __shfl_sync(~0u, pick4(s0, s1, s2, s3, j), qi);
+      const uint32_t ls = (uint32_t)(((unsigned long long)x * n_loc) >> 32);
+      const uint32_t D = P.d_full ? ~0u : lt, A = dec & corr;
+      if (ls != 0u && ls + 2u < n_loc) {
+        // the common case: all four sites in the thread's own column, no rotation
+        uint32_t *p = lat + ls * S_w + w;
+        uint32_t a = p[0u - S_w], b0 = p[0], b1 = p[S_w], cc = p[2u * S_w];
+        paper_bond(a, b0, b1, cc, D, A, fis);
+        p[0u - S_w] = a;
+        p[0] = b0;
+        p[S_w] = b1;
+        p[2u * S_w] = cc;
+      } else {
+        paper_barrier(bar, S_w);
+        paper_step_cross(lat, n_loc, S_w, w, w_lo, rot_lo, w_hi, rot_hi, ls, D, A, fis);
+        paper_barrier(bar, S_w);
       }
     }
+  };
+
+  if (begin < end) {
+    const uint32_t q1 = (end - 1u) >> 2;
+    const bool head = (begin & 3u) != 0u || q0 == q1;
+    uint32_t q = q0;
+    if (head) group(q++, PaperEdge<true>{});
+    const uint32_t q_full_end = ((end & 3u) == 0u) ? q1 + 1u : q1;  // groups entirely inside
+    for (; q < q_full_end; ++q) group(q, PaperEdge<false>{});
+    if (q <= q1) group(q, PaperEdge<true>{});
   }
-  if (r < P.n_rec && P.rec_step[r] == (unsigned long long)end) paper_record(P, lat, w, sys, r++);
+  if (r < P.n_rec && P.rec_step[r] == (unsigned long long)end) paper_record(P, lat, w, sys, r);
   for (uint32_t i = w; i < words; i += S_w) __stcg(glat + i, lat[i]);
 }
 
