@@ -38,12 +38,22 @@ TRAFFIC_PER_LAUNCH = 39.11e6 + 794.56e6
 UNIT = "attempts/s"
 
 
+# Integer pipe rates per SM and clock on this GPU: 32-bit logic / compare / shift (LOP3 and
+# kin) on the 64-lane ALU pipe; 32x32->64-bit multiplies (Philox's mul.wide) at 32 per clock
+# on the FMA pipe.  Both agree with the documented per-SM integer throughputs and with a
+# microbenchmark (independent chains: LOP3 and IMAD 60, IMAD.WIDE 24-32, IADD 119, FFMA 115
+# per SM per clock at 2.07 GHz; Philox4x32-10 alone 5.05e11 blocks/s = 32 wide multiplies).
+LOGIC_LANES = 64
+WIDE_MUL_LANES = 32
+
+
 def algorithmic_ops_per_item(t_d: int, t_da: int):
-    """Algorithmic integer operations per (window, 32-sample group) item of the method:
-    40 per Philox4x32-10 block (10 rounds x (2 wide multiplies + 2 three-input XORs)) times
-    the expected number of blocks under the per-item MSB-first early exit, 2 per expected
-    plane (one three-input logic op per plane per threshold), 11 for the window logic and 6
-    shared-memory loads/stores.  Returns (ops, expected blocks, expected planes)."""
+    """Algorithmic integer operations per (window, 32-sample group) item of the method.
+    Philox4x32-10: per block 10 rounds x (2 wide multiplies + 2 three-input XORs), times the
+    expected number of blocks under the per-item MSB-first early exit; compare: one
+    three-input logic op per plane per threshold (2 per expected plane); window logic 11 ops;
+    6 shared-memory loads/stores.  Returns (all ops, expected blocks, expected planes,
+    wide multiplies, logic-pipe ops)."""
     two32 = 1 << 32
 
     def p_open(k):  # P(the item is still undecided after k planes)
@@ -57,7 +67,25 @@ def algorithmic_ops_per_item(t_d: int, t_da: int):
         return 1.0 - (1.0 - len(cells) * 2.0 ** -k) ** 32
     planes = sum(p_open(k) for k in range(32))
     blocks = 1.0 + sum(p_open(k) for k in (3, 7, 11, 15, 19, 23, 27, 31))
-    return 40.0 * blocks + 2.0 * planes + 11.0 + 6.0, blocks, planes
+    mul = 20.0 * blocks
+    logic = 20.0 * blocks + 2.0 * planes + 11.0
+    return mul + logic + 6.0, blocks, planes, mul, logic
+
+
+def pipe_roofline(items_per_s: float, mul_per_item: float, logic_per_item: float, sm_count: int,
+                  mhz: float) -> dict:
+    """Fractions of the two integer pipes the work needs; the larger one binds."""
+    peak_mul = sm_count * WIDE_MUL_LANES * mhz * 1e6
+    peak_logic = sm_count * LOGIC_LANES * mhz * 1e6
+    f_mul = items_per_s * mul_per_item / peak_mul
+    f_logic = items_per_s * logic_per_item / peak_logic
+    if f_mul >= f_logic:
+        return {"achieved": items_per_s * mul_per_item / 1e12, "peak": peak_mul / 1e12,
+                "unit": "T wide-multiply ops/s", "frac": f_mul, "binding_pipe": "32x32->64 multiply (FMA pipe)",
+                "frac_logic_pipe": f_logic}
+    return {"achieved": items_per_s * logic_per_item / 1e12, "peak": peak_logic / 1e12,
+            "unit": "T logic ops/s", "frac": f_logic, "binding_pipe": "32-bit logic (ALU pipe)",
+            "frac_wide_multiply_pipe": f_mul}
 
 
 class ClockSampler:
@@ -235,14 +263,17 @@ def stream_leg(pcpd, substeps: int = 2048):
             "hbm_gbs_algorithmic": hbm, "hbm_frac_of_measured_copy": hbm / 6787.2}
 
 
-def paper_ops_per_step_thread(m: int, n_dec: int) -> float:
-    """Algorithmic integer operations per (step, thread) of the paper's scheme: 40 per
-    Philox4x32-10 block ((m + n_dec + 2)/4 mask blocks, as four steps share whole blocks, and
-    1/128 of a local-site block), 2 per diffusion plane, 1 per decorrelation word, 2 for the
-    broadcast compare, 12 for the bond logic of Alg. 2 and 8 shared-memory loads/stores.
-    One (step, thread) = 32 attempts."""
+def paper_ops_per_step_thread(m: int, n_dec: int):
+    """Algorithmic integer operations per (step, thread) of the paper's scheme: Philox4x32-10
+    blocks ((m + n_dec + 2)/4 mask blocks, as four steps share whole blocks, and 1/128 of a
+    local-site block) at 20 wide multiplies + 20 three-input XORs each; 2 logic ops per
+    diffusion plane, 1 per decorrelation word, 2 for the broadcast compare, 12 for the bond
+    logic of Alg. 2; 8 shared-memory loads/stores.  One (step, thread) = 32 attempts.
+    Returns (all ops, blocks, wide multiplies, logic-pipe ops)."""
     blocks = (m + n_dec + 2) / 4.0 + 1.0 / 128.0
-    return 40.0 * blocks + 2.0 * m + n_dec + 2.0 + 12.0 + 8.0, blocks
+    mul = 20.0 * blocks
+    logic = 20.0 * blocks + 2.0 * m + n_dec + 2.0 + 12.0
+    return mul + logic + 8.0, blocks, mul, logic
 
 
 def paper_leg(pcpd, mcs: int = 1000, systems: int = 3648):
@@ -254,7 +285,8 @@ def paper_leg(pcpd, mcs: int = 1000, systems: int = 3648):
     import torch
     out = []
     m, n_dec = 1, 2
-    ops, blocks = paper_ops_per_step_thread(m, n_dec)
+    ops, blocks, mul, logic = paper_ops_per_step_thread(m, n_dec)
+    sm_count = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     for n_loc, S_w in ((32, 64), (64, 32)):
         L = 32 * n_loc * S_w
         stream = torch.cuda.Stream()
@@ -273,11 +305,8 @@ def paper_leg(pcpd, mcs: int = 1000, systems: int = 3648):
         out.append({"n_loc": n_loc, "S_w": S_w, "L": L, "systems": systems, "mcs": mcs,
                     "value": rate, "unit": UNIT, "ms": ms, "plan": h.plan(),
                     "rho_end": float(h.density()[-1]),
-                    "roofline": {"bound": "alu", "achieved": ops * step_threads / 1e12,
-                                 "peak": 40.27392, "unit": "Tops/s",
-                                 "frac": ops * step_threads / 40.27392e12,
-                                 "ops_per_step_thread": ops,
-                                 "frac_of_philox_pipe_cap": rate / (5.05e11 * 32.0 / blocks)}})
+                    "roofline": {"bound": "alu", **pipe_roofline(step_threads, mul, logic, sm_count, 2070.0),
+                                 "ops_per_step_thread": ops, "philox_blocks_per_step_thread": blocks}})
         h.close()
     return {"workload": "paper scheme, L=65536, %d systems, d=0.5 (m=1), n_dec=2, p=0.15, %d MCS"
             % (systems, mcs), "runs": out,
@@ -432,7 +461,7 @@ def main():
     (attempts_all,), (ms_max,) = combine(dist, [attempts], [ms], device="cuda")
     value = attempts_all / (ms_max / 1e3)
 
-    # roofline of the dominant kernel (the tile sweep): integer issue slots
+    # roofline of the dominant kernel (the tile sweep): the binding integer pipe
     props = torch.cuda.get_device_properties(local)
     sm_count = props.multi_processor_count
     peaks = {}
@@ -441,22 +470,21 @@ def main():
     except Exception:
         pass
     sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = sm_count * 4 * 32 * sm_max_mhz * 1e6 / 1e12   # T lane-ops/s
-    achieved = (alg_ops / (ms / 1e3)) / 1e12
+    items = [S // 32 * K_win * n for n in subs]            # (window, group) items, this rank
+    items_s = sum(items) / (ms / 1e3)
+    mul_item = sum(i * o[3] for i, o in zip(items, ops_item)) / sum(items)
+    logic_item = sum(i * o[4] for i, o in zip(items, ops_item)) / sum(items)
     plan0 = sims[0].plan()
     kname = "pcpd_jit_sweep (engine compiled for the run's thresholds)" if plan0.get("jit") else "k_sweep_persistent"
-    # Pipe-aware ceiling of the same work (measured on this GPU): Philox's 32x32->64 multiplies
-    # run at 1/4 of the issue rate on the FMA pipe (5.05e11 Philox blocks/s), so at the
-    # method's expected blocks per item the attempt rate cannot exceed 5.05e11*32/blocks.
-    philox_cap = sum(5.05e11 * 32.0 / o[1] for o in ops_item) / len(ops_item)
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                "frac": achieved / peak,
+    issue_peak = sm_count * 4 * 32 * sm_max_mhz * 1e6 / 1e12   # T lane-ops/s, all pipes together
+    roofline = {"bound": "alu", **pipe_roofline(items_s, mul_item, logic_item, sm_count, sm_max_mhz),
                 "traffic": TRAFFIC_PER_LAUNCH if plan0.get("jit") else None,
                 "kernel": f"{kname}; tiles {plan0['core']}+2x{plan0['halo']} sites, tau={plan0['tau']}",
-                "peak_note": f"{sm_count} SMs x 4 SMSPs x 32 lanes x {sm_max_mhz:.0f} MHz issue slots (derived)",
-                "ops_per_attempt": [round(o[0] / 32, 3) for o in ops_item],
-                "philox_pipe_cap_attempts_per_s": philox_cap,
-                "frac_of_philox_pipe_cap": value / world / philox_cap}
+                "peak_note": f"{sm_count} SMs x {WIDE_MUL_LANES} wide-multiply / {LOGIC_LANES} logic lanes x "
+                             f"{sm_max_mhz:.0f} MHz (derived; lane rates measured, see DESIGN.md)",
+                "wide_multiplies_per_item": round(mul_item, 2), "logic_ops_per_item": round(logic_item, 2),
+                "expected_philox_blocks_per_item": [round(o[1], 3) for o in ops_item],
+                "frac_of_issue_slots": (alg_ops / (ms / 1e3)) / 1e12 / issue_peak}
 
     # end to end through the public API with host buffers (pinned), host<->device in the region
     e2e = None

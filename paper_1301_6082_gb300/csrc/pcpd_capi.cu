@@ -351,9 +351,12 @@ int make_plan(pcpd_t *h, const pcpd_params *prm) {
     } else {
       const size_t max_core = avail_words > 2u * h->halo ? avail_words - 2u * h->halo : 0;
       if (max_core < 1024) return fail(PCPD_EINVAL, "temporal block tau=%u too large for shared memory", h->tau);
-      const uint32_t nseg = (uint32_t)((L + max_core - 1) / max_core);
-      core = (L + nseg - 1) / nseg;
-      core = (core + 3u) & ~3u;   // keep tile starts 16-byte aligned
+      uint32_t nseg = (uint32_t)((L + max_core - 1) / max_core);
+      for (;; ++nseg) {
+        core = (L + nseg - 1) / nseg;
+        core = (core + 3u) & ~3u;   // keep tile starts 16-byte aligned
+        if (core <= max_core) break;   // the rounding may push a tile past the budget
+      }
     }
     h->core = core;
     h->n_seg = (L + core - 1) / core;

@@ -308,3 +308,14 @@ def test_substep_counter_near_its_limit(P, oracle_mod):
     np.testing.assert_array_equal(sim.lattice(), oracle_mod.pack(st))
     with pytest.raises(P.PcpdError):
         sim.run_substeps(2)
+
+
+def test_plans_exist_for_every_lattice_size_near_the_shared_memory_limit(P):
+    """Every L from ring-sized through a few segments gets a plan that fits (the 16-byte
+    rounding of segment cores must not push a tile past the budget), and runs."""
+    for L in list(range(30011, 80000, 997)) + [39328, 39329, 39330, 78655, 78660]:
+        with P.Pcpd(L, 32, 0.15, 0.5, seed=2, jit=-1) as sim:
+            sim.run_substeps(3)
+            sim.sync()
+            plan = sim.plan()
+            assert plan["ring"] == 1 or plan["core"] + 2 * plan["halo"] <= 60000
