@@ -1884,8 +1884,9 @@ PaperKernel paper_kernel_m(uint32_t nd) {
   }
 }
 
-PaperKernel paper_kernel(uint32_t m, uint32_t nd, uint32_t threads, int generic) {
-  if (threads > 256) return pcpdk::k_paper_sweep<-1, 0, 1024>;
+PaperKernel paper_kernel(uint32_t m, uint32_t nd, uint32_t threads, uint32_t S_w, uint32_t spc, int generic) {
+  // the small-CTA kernels hold one system per CTA unless a system is one warp
+  if (threads > 256 || (S_w > 32 && spc > 1)) return pcpdk::k_paper_sweep<-1, 0, 1024>;
   if (generic) return pcpdk::k_paper_sweep<-1, 0, 256>;
   switch (m) {
     case 0: return paper_kernel_m<0>(nd);
@@ -1983,7 +1984,7 @@ int pcpd_paper_create(const pcpd_paper_params *prm, pcpd_paper_t **out) {
                 (unsigned long long)words, optin);
   uint32_t spc = prm->plan_spc;
   if (spc == 0) {
-    spc = prm->S_w >= 256 ? 1u : 256u / prm->S_w;
+    spc = prm->S_w > 32 ? 1u : 8u;   // systems of several warps: one per CTA (CTA barrier)
     while (spc > 1 && spc * words * 4 > (uint64_t)optin) --spc;
   }
   if (spc > 15 || spc * prm->S_w > 1024 || spc * words * 4 > (uint64_t)optin)
@@ -2010,7 +2011,7 @@ int pcpd_paper_create(const pcpd_paper_params *prm, pcpd_paper_t **out) {
   h->threads = spc * h->S_w;
   h->grid = (h->systems + spc - 1) / spc;
   h->smem = (size_t)spc * words * 4;
-  h->kernel = paper_kernel(h->m, h->n_dec, h->threads, prm->generic);
+  h->kernel = paper_kernel(h->m, h->n_dec, h->threads, h->S_w, h->spc, prm->generic);
   rc = paper_smem_optin(h->kernel, h->smem);
   if (rc) return bail(rc);
   if (prm->stream) {

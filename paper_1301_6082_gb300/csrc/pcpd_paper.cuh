@@ -53,10 +53,16 @@ struct PaperParams {
   uint32_t systems_total;                 // row length of rec_sys
 };
 
-// The S_w threads of one system meet (id: 1 + the system's slot in the CTA).
+// The S_w threads of one system meet.  One warp: __syncwarp.  Kernels for CTAs of up to 256
+// threads hold a single system when it spans several warps, and use the CTA barrier: a named
+// barrier with a run-time id would reserve all 16 of the CTA's hardware barriers and cap
+// residency at 4 CTAs per SM.  Larger CTAs: named barrier 1 + the system's slot.
+template <int MAXT>
 __device__ __forceinline__ void paper_barrier(uint32_t id, uint32_t nthreads) {
   if (nthreads == 32u)
     __syncwarp();
+  else if (MAXT <= 256)
+    __syncthreads();
   else
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
@@ -212,9 +218,9 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 6 : 1) k_paper_sweep(const
         p[S_w] = b1;
         p[2u * S_w] = cc;
       } else {
-        paper_barrier(bar, S_w);
+        paper_barrier<MAXT>(bar, S_w);
         paper_step_cross(lat, n_loc, S_w, w, w_lo, rot_lo, w_hi, rot_hi, ls, D, A, fis);
-        paper_barrier(bar, S_w);
+        paper_barrier<MAXT>(bar, S_w);
       }
     }
   };
