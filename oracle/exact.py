@@ -14,7 +14,8 @@ Two discrete-time chains, both written from the paper (Schram, arXiv 1301.6082):
 * ``sched_*`` -- the random-phase 3-site window schedule (R2 of the design): sub-step =
   sum over phases phi (weight w_phi) of the product of independent 3-site kernels on the
   windows (phi+3k, phi+3k+1, phi+3k+2), k < K = floor(L/3); leftover sites idle.  MCS time t
-  is sub-step ceil(t*L/K).
+  is sub-step ceil(t*L/K).  The same with windows of n+1 sites for the n-tuple processes
+  (TCPD n = 3, QCPD n = 4; R14).
 
 Probabilities come from the integer thresholds exactly: P_D = T_D/2^32,
 P_A = (T_DA - T_D)/2^32, P_F = 1 - T_DA/2^32 (window form); P_P = T_P/2^32 (Alg. 1 form).
@@ -76,18 +77,51 @@ def window_kernel(pD: float, pA: float) -> np.ndarray:
     return K
 
 
-def sched_substep(v: np.ndarray, L: int, t_d: int, t_da: int, phase_w=None) -> np.ndarray:
+def tuple_window_kernel(pD: float, pA: float, n: int) -> np.ndarray:
+    """Kernel of one window of W = n+1 sites for the n-tuple process (R14): local index bit
+    W-1-j is site w_j.  Orientation o (1/2 each): o = 0 takes the tuple w_0..w_{n-1}, the
+    bond (w_0, w_1) and the target w_n; o = 1 the tuple w_1..w_n, the bond (w_1, w_2) and the
+    target w_0.  Diffusion (pD) swaps the bond; otherwise, on a fully occupied tuple,
+    annihilation (pA) empties it and fission (1-pD-pA) fills the target."""
+    W = n + 1
+    pF = 1.0 - pD - pA
+    K = np.zeros((1 << W, 1 << W))
+    for old in range(1 << W):
+        s0 = [(old >> (W - 1 - j)) & 1 for j in range(W)]
+        for o in (0, 1):
+            tup = list(range(1, W)) if o else list(range(0, n))
+            b0 = tup[0]
+            tgt = 0 if o else n
+            for cls, pr in (("D", pD), ("A", pA), ("F", pF)):
+                s = list(s0)
+                if cls == "D":
+                    s[b0], s[b0 + 1] = s[b0 + 1], s[b0]
+                elif all(s[j] == 1 for j in tup):
+                    if cls == "A":
+                        for j in tup:
+                            s[j] = 0
+                    else:
+                        s[tgt] = 1
+                new = sum(b << (W - 1 - j) for j, b in enumerate(s))
+                K[new, old] += 0.5 * pr
+    return K
+
+
+def sched_substep(v: np.ndarray, L: int, t_d: int, t_da: int, phase_w=None, n: int = 2) -> np.ndarray:
+    """One sub-step of the window schedule: windows of W = n+1 sites (n = 2: the PCPD's
+    3-site windows with the kernel above), K = floor(L/W) of them at each phase."""
     pD = t_d / TWO32
     pA = (t_da - t_d) / TWO32
-    K3 = window_kernel(pD, pA)
-    nwin = L // 3
+    W = n + 1
+    Kw = window_kernel(pD, pA) if n == 2 else tuple_window_kernel(pD, pA, n)
+    nwin = L // W
     w = index_weights(L) if phase_w is None else phase_w
     out = np.zeros_like(v)
     for phi in range(L):
         u = v
         for k in range(nwin):
-            sites = [(phi + 3 * k + r) % L for r in range(3)]
-            u = _apply_local(u, L, sites, K3)
+            sites = [(phi + W * k + r) % L for r in range(W)]
+            u = _apply_local(u, L, sites, Kw)
         out += w[phi] * u
     return out
 
@@ -197,15 +231,16 @@ def start_vector(L: int, mode: str = "full") -> np.ndarray:
     return v
 
 
-def sched_moments(L: int, t_d: int, t_da: int, rec_sub, mode: str = "full"):
-    """Exact E[rho] and Var[rho] of one sample after each sub-step count in rec_sub."""
+def sched_moments(L: int, t_d: int, t_da: int, rec_sub, mode: str = "full", tuple_n: int = 2):
+    """Exact E[rho] and Var[rho] of one sample after each sub-step count in rec_sub
+    (tuple_n: 2 PCPD, 3 TCPD, 4 QCPD)."""
     occ = occupation(L)
     v = start_vector(L, mode)
     w = index_weights(L)
     mean, var, n = [], [], 0
     for r in rec_sub:
         while n < r:
-            v = sched_substep(v, L, t_d, t_da, w)
+            v = sched_substep(v, L, t_d, t_da, w, tuple_n)
             n += 1
         m1 = float(v @ occ) / L
         m2 = float(v @ (occ * occ)) / (L * L)

@@ -49,12 +49,15 @@ def lib():
             L.orc_thresholds.restype = C.c_int
             L.orc_substep_of_time.argtypes = [C.c_uint32, C.c_uint64]
             L.orc_substep_of_time.restype = C.c_uint64
+            L.orc_substep_of_time_w.argtypes = [C.c_uint32, C.c_uint32, C.c_uint64]
+            L.orc_substep_of_time_w.restype = C.c_uint64
             L.orc_phase.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32]
             L.orc_phase.restype = C.c_uint32
             L.orc_init.argtypes = [u8p, C.c_uint32, C.c_uint32, C.c_int, C.c_uint64, C.c_uint32]
             L.orc_init.restype = C.c_int
             L.orc_run.argtypes = [C.c_uint32, C.c_uint32, C.c_uint64, C.c_uint64, C.c_uint64, u8p,
-                                  C.c_uint64, C.c_uint64, u64p, C.c_uint32, u64p, u32p, u64p, C.c_int, C.c_uint32, u64p]
+                                  C.c_uint64, C.c_uint64, u64p, C.c_uint32, u64p, u32p, u64p, C.c_int, C.c_uint32, u64p,
+                                  C.c_uint32]
             L.orc_run.restype = C.c_int
             L.orc_rs_run.argtypes = [C.c_uint32, C.c_uint32, C.c_uint64, C.c_uint64, C.c_uint64, u8p,
                                      C.c_uint64, C.c_uint64, u64p, C.c_uint32, u64p, u32p, C.c_int]
@@ -89,8 +92,11 @@ def thresholds(p: float, d: float):
     return int(td.value), int(tda.value), int(tp.value)
 
 
-def substep_of_time(L: int, t: int) -> int:
-    return int(lib().orc_substep_of_time(L, t))
+def substep_of_time(L: int, t: int, tuple_n: int = 2) -> int:
+    """Sub-step at which MCS time t is reached: ceil(t*L/K), K = floor(L/(n+1))."""
+    if tuple_n == 2:
+        return int(lib().orc_substep_of_time(L, t))
+    return int(lib().orc_substep_of_time_w(L, tuple_n + 1, t))
 
 
 def phase(seed: int, L: int, h: int, n: int) -> int:
@@ -124,9 +130,10 @@ def unpack(words: np.ndarray) -> np.ndarray:
 
 def run(state: np.ndarray, p: float, d: float, seed: int, n_begin: int, n_end: int,
         rec_sub=(), per_sample: bool = False, threads: int | None = None, group0: int = 0,
-        pairs: bool = False):
+        pairs: bool = False, tuple_n: int = 2):
     """Advance ``state`` (modified in place, [S][L] bytes: groups group0, group0+1, ... of an
-    instance) from sub-step n_begin to n_end on the window schedule.
+    instance) from sub-step n_begin to n_end on the window schedule; tuple_n = 2 (PCPD),
+    3 (TCPD) or 4 (QCPD), windows of tuple_n + 1 sites.
     Returns (totals u64[R], per-sample u32[R][S] or None, events[3]), plus the occupied
     nearest-neighbour pair counts u64[R] as a fourth element when ``pairs``."""
     assert state.dtype == np.uint8 and state.flags.c_contiguous
@@ -141,9 +148,9 @@ def run(state: np.ndarray, p: float, d: float, seed: int, n_begin: int, n_end: i
     rc = lib().orc_run(L, S, td, tda, C.c_uint64(seed), _p(state, C.c_uint8), n_begin, n_end,
                        _p(rec, C.c_uint64), len(rec), _p(tot, C.c_uint64),
                        _p(ps, C.c_uint32) if ps is not None else None, _p(ev, C.c_uint64), nt, group0,
-                       _p(prs, C.c_uint64))
+                       _p(prs, C.c_uint64), tuple_n)
     if rc == 2:
-        raise AssertionError("oracle: a window changed the particle number by other than +1, -2, 0")
+        raise AssertionError("oracle: a window changed the particle number by other than +1, -n, 0")
     if rc != 0:
         raise ValueError("oracle: bad arguments")
     if pairs:

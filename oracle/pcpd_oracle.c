@@ -103,13 +103,19 @@ int orc_thresholds(double p, double d, uint64_t *t_d, uint64_t *t_da, uint64_t *
     return 0;
 }
 
-/* Time: after n sub-steps a sample has had n*K attempts, K = floor(L/3); MCS time t
- * (t*L attempts) is reached at sub-step ceil(t*L/K). */
-uint64_t orc_substep_of_time(uint32_t L, uint64_t t)
+/* Time: after n sub-steps a sample has had n*K attempts, K = floor(L/W) windows of W sites
+ * (W = 3 for the PCPD, W = n+1 for n-tuples); MCS time t (t*L attempts) is reached at
+ * sub-step ceil(t*L/K). */
+uint64_t orc_substep_of_time_w(uint32_t L, uint32_t W, uint64_t t)
 {
-    unsigned __int128 K = L / 3u;
+    unsigned __int128 K = L / W;
     unsigned __int128 num = (unsigned __int128)t * L;
     return (uint64_t)((num + K - 1) / K);
+}
+
+uint64_t orc_substep_of_time(uint32_t L, uint64_t t)
+{
+    return orc_substep_of_time_w(L, 3u, t);
 }
 
 /* Random phase of sub-step n for phase group h: phi = floor(x0 * L / 2^32). */
@@ -145,37 +151,47 @@ int orc_init(uint8_t *state, uint32_t L, uint32_t S, int mode, uint64_t seed, ui
 }
 
 /* ---------------------------------------------------------------------------------------
- * One window update for one sample (Alg. 1's decision tree on the bond the orientation
- * picks; Eq. (1) rates through R3's thresholds).  Sites a, b, c are consecutive.
- *   o = 0: bond (a, b), fission target c   (Alg. 1 "fission high")
- *   o = 1: bond (b, c), fission target a   (Alg. 1 "fission low")
- * u < T_D: diffusion swaps the bond; else if both bond sites are occupied:
- * u < T_DA annihilates them, otherwise the target becomes occupied.
- * Returns the change in particle number (checked to be one of +1, -2, 0).
+ * One window update for one sample: Alg. 1's decision tree (Eq. (1) rates through R3's
+ * thresholds) on the tuple the orientation picks, for n-tuples (n = 2 is the PCPD; n = 3, 4
+ * the TCPD and QCPD of R14).  site[0..n] are the W = n+1 consecutive sites of the window.
+ *   o = 0: tuple site[0..n-1], diffusion bond (site[0], site[1]), fission target site[n]
+ *          (Alg. 1 "fission high")
+ *   o = 1: tuple site[1..n], diffusion bond (site[1], site[2]), fission target site[0]
+ *          (Alg. 1 "fission low")
+ * u < T_D: diffusion swaps the bond; else if all n tuple sites are occupied: u < T_DA empties
+ * them, otherwise the target becomes occupied.  For n = 2: bond (a, b) -> target c, or bond
+ * (b, c) -> target a.  Returns the change in particle number (one of +1, -n, 0).
  * ------------------------------------------------------------------------------------- */
-static int orc_window(uint8_t *sa, uint8_t *sb, uint8_t *sc, uint32_t o, uint64_t u,
+static int orc_window(uint8_t *row, const uint32_t *site, uint32_t n, uint32_t o, uint64_t u,
                       uint64_t t_d, uint64_t t_da)
 {
-    uint8_t *q = o ? sc : sa; /* the pair partner of b */
-    uint8_t *t = o ? sa : sc; /* the fission target    */
-    int before = *sa + *sb + *sc;
+    const uint32_t first = o ? 1u : 0u;          /* the tuple's first site */
+    const uint32_t target = o ? 0u : n;
+    int before = 0;
+    for (uint32_t j = 0; j <= n; ++j) before += row[site[j]];
     if (u < t_d) {
-        uint8_t tmp = *sb;
-        *sb = *q;
-        *q = tmp;
-    } else if (*sb == 1 && *q == 1) {
-        if (u < t_da) {
-            *sb = 0;
-            *q = 0;
-        } else {
-            *t = 1;
+        uint8_t tmp = row[site[first]];
+        row[site[first]] = row[site[first + 1]];
+        row[site[first + 1]] = tmp;
+    } else {
+        uint32_t occupied = 0;   /* occupied sites of the tuple */
+        for (uint32_t j = 0; j < n; ++j) occupied += row[site[first + j]];
+        if (occupied == n) {
+            if (u < t_da) {
+                for (uint32_t j = 0; j < n; ++j) row[site[first + j]] = 0;
+            } else {
+                row[site[target]] = 1;
+            }
         }
     }
-    return *sa + *sb + *sc - before;
+    int after = 0;
+    for (uint32_t j = 0; j <= n; ++j) after += row[site[j]];
+    return after - before;
 }
 
 typedef struct {
     uint32_t L, S;
+    uint32_t n;            /* tuple size: 2 PCPD, 3 TCPD, 4 QCPD; windows of n+1 sites */
     uint64_t t_d, t_da, seed;
     uint8_t *state;
     uint64_t n_begin, n_end;
@@ -188,7 +204,7 @@ typedef struct {
     pthread_mutex_t *mu;
     uint32_t g_begin, g_end;
     uint32_t g0;           /* group index of the state's first group (keys and phase groups) */
-    int bad;               /* set if a window changed N by something other than +1,-2,0 */
+    int bad;               /* set if a window changed N by something other than +1, -n, 0 */
 } orc_job;
 
 /* Record r: occupied sites, and occupied nearest-neighbour pairs (i, i+1 mod L) -- the pair
@@ -212,7 +228,7 @@ static void orc_count(orc_job *jb, uint32_t g, uint32_t r, uint64_t *tot, uint64
 static void *orc_worker(void *arg)
 {
     orc_job *jb = (orc_job *)arg;
-    const uint32_t L = jb->L, K = L / 3u;
+    const uint32_t L = jb->L, n_tup = jb->n, W = n_tup + 1u, K = L / W;
     uint64_t *tot = (uint64_t *)calloc(jb->n_rec ? jb->n_rec : 1, sizeof(uint64_t));
     uint64_t *prs = (uint64_t *)calloc(jb->n_rec ? jb->n_rec : 1, sizeof(uint64_t));
     uint64_t ev[3] = {0, 0, 0};
@@ -233,21 +249,22 @@ static void *orc_worker(void *arg)
                     orc_block(jb->seed, k, (uint32_t)n, gk, (ORC_TAG_DYN << 28) | b, words + 4 * b);
                 const uint32_t O = words[0];
                 /* plane P_m is words[32 - m] for m = 31..0 */
-                const uint32_t ia = (uint32_t)(((uint64_t)phi + 3ull * k) % L);
-                const uint32_t ib = (uint32_t)(((uint64_t)phi + 3ull * k + 1) % L);
-                const uint32_t ic = (uint32_t)(((uint64_t)phi + 3ull * k + 2) % L);
+                uint32_t site[8];
+                for (uint32_t q = 0; q < W; ++q)
+                    site[q] = (uint32_t)(((uint64_t)phi + (uint64_t)W * k + q) % L);
                 for (uint32_t j = 0; j < 32; ++j) {
                     uint64_t u = 0;
                     for (int m = 31; m >= 0; --m)
                         u |= (uint64_t)((words[32 - m] >> j) & 1u) << m;
                     const uint32_t o = (O >> j) & 1u;
                     uint8_t *row = jb->state + (uint64_t)(32u * g + j) * L;
-                    uint8_t before_b = row[ib], before_q = o ? row[ic] : row[ia];
-                    int dn = orc_window(row + ia, row + ib, row + ic, o, u, jb->t_d, jb->t_da);
-                    if (dn != 0 && dn != 1 && dn != -2) jb->bad = 1;
-                    if (dn == -2) ev[1]++;
+                    const uint32_t first = o ? 1u : 0u;
+                    const int moved = row[site[first]] != row[site[first + 1]];
+                    int dn = orc_window(row, site, n_tup, o, u, jb->t_d, jb->t_da);
+                    if (dn != 0 && dn != 1 && dn != -(int)n_tup) jb->bad = 1;
+                    if (dn == -(int)n_tup) ev[1]++;
                     else if (dn == 1) ev[2]++;
-                    else if (u < jb->t_d && before_b != before_q) ev[0]++;
+                    else if (u < jb->t_d && moved) ev[0]++;
                 }
             }
         }
@@ -271,14 +288,17 @@ static void *orc_worker(void *arg)
  * is counted into rec_total[r] (+= over all samples), rec_sample[r][s] (if non-NULL) and the
  * occupied nearest-neighbour pairs into rec_pairs[r] (if non-NULL).
  * events (nullable, [3]) accumulates moving swaps, annihilations and fissions.
+ * tuple: n = 2 (PCPD; 0 means 2), 3 (TCPD) or 4 (QCPD): windows of n+1 sites (R14).
  * Returns 0, or 1 on bad arguments, or 2 if the particle-number invariant failed.
  */
 int orc_run(uint32_t L, uint32_t S, uint64_t t_d, uint64_t t_da, uint64_t seed,
             uint8_t *state, uint64_t n_begin, uint64_t n_end, const uint64_t *rec_sub,
             uint32_t n_rec, uint64_t *rec_total, uint32_t *rec_sample, uint64_t *events,
-            int n_threads, uint32_t g0, uint64_t *rec_pairs)
+            int n_threads, uint32_t g0, uint64_t *rec_pairs, uint32_t tuple)
 {
-    if (L < 3 || S % 32u || n_end < n_begin || n_end > 0xFFFFFFFFull) return 1;
+    if (tuple == 0) tuple = 2u;
+    if (tuple < 2u || tuple > 4u || L < tuple + 1u || S % 32u || n_end < n_begin || n_end > 0xFFFFFFFFull)
+        return 1;
     const uint32_t G = S / 32u;
     if (n_threads < 1) n_threads = 1;
     if ((uint32_t)n_threads > G) n_threads = (int)G;
@@ -292,7 +312,7 @@ int orc_run(uint32_t L, uint32_t S, uint64_t t_d, uint64_t t_da, uint64_t seed,
     pthread_t *th = (pthread_t *)calloc((size_t)n_threads, sizeof(pthread_t));
     for (int t = 0; t < n_threads; ++t) {
         orc_job *jb = &jobs[t];
-        jb->L = L; jb->S = S; jb->t_d = t_d; jb->t_da = t_da; jb->seed = seed;
+        jb->L = L; jb->S = S; jb->n = tuple; jb->t_d = t_d; jb->t_da = t_da; jb->seed = seed;
         jb->state = state; jb->n_begin = n_begin; jb->n_end = n_end;
         jb->rec_sub = rec_sub; jb->n_rec = n_rec; jb->rec_total = rec_total;
         jb->rec_sample = rec_sample; jb->events = events; jb->mu = &mu;

@@ -92,3 +92,20 @@ def test_pack_roundtrip(oracle_mod):
     # random-half init: bit j of group g's word at site i is the INIT Philox word's bit j
     ctr = np.array([[i, 0, g, 2 << 28] for g in range(3) for i in range(33)], dtype=np.uint32)
     np.testing.assert_array_equal(w.reshape(-1), oracle_mod.philox(ctr, 2)[:, 0])
+
+
+def test_oracle_still_writes_the_stored_golden_run(oracle_mod):
+    """Regression guard for refactors of the oracle: the stored L=1024, 64-sample decay run
+    (written by tests/golden/make_golden.py from an earlier oracle) is reproduced."""
+    import os
+    from paper_1301_6082_gb300.workloads import SMALL_L1024, log_times
+    w = SMALL_L1024
+    L, S = w["L"], w["S"]
+    d, p = w["runs"][0]
+    ts = log_times(w["mcs"], w["n_rec"])
+    sub = [oracle_mod.substep_of_time(L, t) for t in ts]
+    st = oracle_mod.init_state(L, S, w["init"], w["seed"])
+    tot, _, _ = oracle_mod.run(st, p, d, w["seed"], 0, sub[-1], sub)
+    golden = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "pcpd_L1024_S64.txt"), dtype=np.uint64)
+    np.testing.assert_array_equal(golden[:, 1], np.array(sub, dtype=np.uint64))
+    np.testing.assert_array_equal(golden[:, 2], tot)

@@ -12,21 +12,28 @@ import tests.test_oracle_exact as TE
 import tests.test_oracle_invariants as TI
 import tests.test_oracle_philox as TP
 import tests.test_oracle_thresholds as TT
+import tests.test_oracle_tuples as TU
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "pcpd_oracle.c")
 
 MUTANTS = {
     "philox_nine_rounds": ("round < 10", "round < 9"),
-    "fission_target_is_partner": ("uint8_t *t = o ? sa : sc;", "uint8_t *t = o ? sc : sa;"),
-    "annihilate_without_pair": ("} else if (*sb == 1 && *q == 1) {\n        if (u < t_da)",
-                                "} else if (*sb == 1 || *q == 1) {\n        if (u < t_da)"),
+    "fission_target_is_partner": ("const uint32_t target = o ? 0u : n;", "const uint32_t target = o ? n : 0u;"),
+    "annihilate_without_pair": ("if (occupied == n) {", "if (occupied >= 1u) {"),
     "rate_p_not_p_times_1_minus_d": ("double scaled_a = p * (1.0 - d);", "double scaled_a = p;"),
     "phase_always_zero": ("return (uint32_t)(((uint64_t)out[0] * (uint64_t)L) >> 32);", "return 0u;"),
-    "windows_cover_wrap": ("const uint32_t L = jb->L, K = L / 3u;", "const uint32_t L = jb->L, K = (L + 2u) / 3u;"),
-    "diffusion_swaps_a_c": ("*sb = *q;\n        *q = tmp;", "*sb = *sb;\n        *sa = *sc; *sc = tmp; (void)q;"),
+    "windows_cover_wrap": ("W = n_tup + 1u, K = L / W;", "W = n_tup + 1u, K = (L + n_tup) / W;"),
+    "diffusion_swaps_a_c": ("uint8_t tmp = row[site[first]];\n        row[site[first]] = row[site[first + 1]];\n"
+                            "        row[site[first + 1]] = tmp;",
+                            "uint8_t tmp = row[site[0]];\n        row[site[0]] = row[site[n]];\n"
+                            "        row[site[n]] = tmp;"),
     "time_floor_not_ceil": ("return (uint64_t)((num + K - 1) / K);", "return (uint64_t)(num / K);"),
     "pair_wrong_neighbour": ("pc += row[i] & row[(i + 1u) % jb->L];", "pc += row[i] & row[(i + 2u) % jb->L];"),
+    # mistakes that only the n-tuple processes (R14) can show
+    "tuple_annihilates_two_sites": ("for (uint32_t j = 0; j < n; ++j) row[site[first + j]] = 0;",
+                                    "for (uint32_t j = 0; j < 2u; ++j) row[site[first + j]] = 0;"),
+    "tuple_target_next_to_pair": ("const uint32_t target = o ? 0u : n;", "const uint32_t target = o ? 0u : 2u;"),
 }
 
 
@@ -62,6 +69,10 @@ def _pins(mod):
     for L in (4, 5, 8, 9):
         yield f"exact_chain_L{L}", (lambda L=L: TE.test_schedule_oracle_matches_exact_chain(mod, L, 0.15, 0.5))
     yield "pair_density_exact_L7", lambda: TE.test_pair_density_matches_exact_chain(mod, 7)
+    for n in (3, 4):
+        yield f"tuple{n}_bookkeeping", (lambda n=n: TU.test_bookkeeping_and_d1_conservation(mod, n))
+        yield f"tuple{n}_closed_form", (lambda n=n: TU.test_p1_d0_first_substep_closed_form(mod, n, 61))
+        yield f"tuple{n}_exact_chain", (lambda n=n: TU.test_schedule_oracle_matches_exact_chain(mod, n, 2 * n))
 
 
 def _caught(mod):
