@@ -72,6 +72,10 @@ typedef struct pcpd_params {
     int jit;                 /* specialise the sweep for this instance's two thresholds by
                                 compiling it at run time (same bits, ~15% faster): 1 = yes,
                                 -1 = no, 0 = automatically for lattices of >= 2^22 words */
+    uint32_t tuple;          /* reacting tuple size n: 0 or 2 = PCPD (pairs, 3-site windows),
+                                3 = TCPD (triplets), 4 = QCPD (quadruplets); windows of n+1
+                                sites, K = floor(L/(n+1)) per sub-step, annihilation empties
+                                the n-tuple (see pcpd_substep_of_time_n) */
 } pcpd_params;
 
 /* Create a simulation of `samples` PCPD samples on a ring of L sites, initialised fully
@@ -163,6 +167,10 @@ int pcpd_thresholds(double p, double d, uint64_t *t_d, uint64_t *t_da);
 
 /* Sub-step at which MCS time t is reached on a ring of L sites: ceil(t*L/floor(L/3)). */
 uint64_t pcpd_substep_of_time(uint32_t L, uint64_t t);
+
+/* The same for the n-tuple processes (tuple as in pcpd_params): ceil(t*L/floor(L/(n+1)));
+ * 0 for an invalid tuple or L shorter than one window. */
+uint64_t pcpd_substep_of_time_n(uint32_t L, uint32_t tuple, uint64_t t);
 
 /* ---- device-level entry points used by the tests (all pointers are device pointers,
  * stream may be NULL for the default stream; the call waits for completion) ---- */

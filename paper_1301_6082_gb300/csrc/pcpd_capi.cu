@@ -78,16 +78,17 @@ int thresholds(double p, double d, uint64_t *td, uint64_t *tda) {
   return PCPD_OK;
 }
 
-// ceil(t*L/K), K = floor(L/3): the sub-step at which MCS time t is reached.
-uint64_t substep_of_time(uint32_t L, uint64_t t) {
-  const unsigned __int128 K = L / 3u;
+// ceil(t*L/K), K = floor(L/W) windows of W sites (3 for the PCPD, n+1 for n-tuples): the
+// sub-step at which MCS time t is reached.
+uint64_t substep_of_time(uint32_t L, uint64_t t, uint32_t W = 3u) {
+  const unsigned __int128 K = L / W;
   const unsigned __int128 num = (unsigned __int128)t * L;
   return (uint64_t)((num + K - 1) / K);
 }
 
 // Largest MCS time reached after n sub-steps: floor(n*K/L).
-uint64_t time_of_substep(uint32_t L, uint64_t n) {
-  return (uint64_t)(((unsigned __int128)n * (L / 3u)) / L);
+uint64_t time_of_substep(uint32_t L, uint64_t n, uint32_t W = 3u) {
+  return (uint64_t)(((unsigned __int128)n * (L / W)) / L);
 }
 
 pcpdk::Thresholds split_thresholds(uint64_t td, uint64_t tda) {
@@ -133,6 +134,7 @@ constexpr size_t kStaticSmem = sizeof(uint32_t) * pcpdk::kPhiChunk + 34 * sizeof
 // ------------------------------------------------------------------------------------------
 struct pcpd {
   uint32_t L = 0, K = 0, S = 0, G = 0, pitch = 0;
+  uint32_t W = 3;             // window width: tuple size + 1
   double p = 0, d = 0;
   uint64_t seed = 0, td = 0, tda = 0;
   pcpdk::Thresholds T{};
@@ -172,19 +174,32 @@ namespace {
 std::mutex g_smem_mu;
 bool g_smem_raised = false;
 
+using SweepKernel = void (*)(const pcpdk::BatchParams);
+
+// The sweep engine for single-instance or batched launches whose instances all have window
+// width W (3, 4, 5), or a batch that mixes them (W = 0: read per instance).
+SweepKernel sweep_kernel(bool batch, uint32_t W) {
+  switch (W) {
+    case 3: return batch ? pcpdk::k_sweep_persistent<true, 3> : pcpdk::k_sweep_persistent<false, 3>;
+    case 4: return batch ? pcpdk::k_sweep_persistent<true, 4> : pcpdk::k_sweep_persistent<false, 4>;
+    case 5: return batch ? pcpdk::k_sweep_persistent<true, 5> : pcpdk::k_sweep_persistent<false, 5>;
+    default: return batch ? pcpdk::k_sweep_persistent<true, 0> : pcpdk::k_sweep_persistent<false, 3>;
+  }
+}
+
 int raise_smem_limit() {
   std::lock_guard<std::mutex> lock(g_smem_mu);
   if (g_smem_raised) return PCPD_OK;
   int optin = 0;
   int rc = smem_optin(&optin);
   if (rc) return rc;
-  cudaFuncAttributes fa0, fa1;
-  CU(cudaFuncGetAttributes(&fa0, pcpdk::k_sweep_persistent<false>));
-  CU(cudaFuncGetAttributes(&fa1, pcpdk::k_sweep_persistent<true>));
-  CU(cudaFuncSetAttribute(pcpdk::k_sweep_persistent<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          optin - (int)fa0.sharedSizeBytes));
-  CU(cudaFuncSetAttribute(pcpdk::k_sweep_persistent<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          optin - (int)fa1.sharedSizeBytes));
+  for (int b = 0; b < 2; ++b)
+    for (uint32_t W : {0u, 3u, 4u, 5u}) {
+      const SweepKernel k = sweep_kernel(b != 0, W);
+      cudaFuncAttributes fa;
+      CU(cudaFuncGetAttributes(&fa, k));
+      CU(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes));
+    }
   g_smem_raised = true;
   return PCPD_OK;
 }
@@ -215,7 +230,7 @@ struct JitApi {
 std::mutex g_jit_mu;
 JitApi g_jit_api;
 bool g_jit_api_tried = false;
-std::map<std::tuple<int, uint32_t, uint32_t>, CUfunction> g_jit;
+std::map<std::tuple<int, uint32_t, uint32_t, uint32_t>, CUfunction> g_jit;
 
 template <typename F>
 bool driver_fn(const char *name, F *out) {
@@ -257,15 +272,16 @@ const JitApi &jit_api() {   // call with g_jit_mu held
   return g_jit_api;
 }
 
-// Compile (once per device and threshold pair) the engine with both thresholds as constants.
-int jit_function(uint32_t td, uint32_t tda, CUfunction *out) {
+// Compile (once per device, threshold pair and window width) the engine with the thresholds
+// and the window width as constants.
+int jit_function(uint32_t td, uint32_t tda, uint32_t W, CUfunction *out) {
   int dev = 0;
   CU(cudaGetDevice(&dev));
   CU(cudaFree(nullptr));   // the runtime's primary context is current for the driver calls
   std::lock_guard<std::mutex> lock(g_jit_mu);
   const JitApi &J = jit_api();
   if (!J.ok) return fail(PCPD_ECUDA, "runtime compiler or driver entry points unavailable");
-  auto key = std::make_tuple(dev, td, tda);
+  auto key = std::make_tuple(dev, td, tda, W);
   auto it = g_jit.find(key);
   if (it != g_jit.end()) {
     *out = it->second;
@@ -274,11 +290,12 @@ int jit_function(uint32_t td, uint32_t tda, CUfunction *out) {
   nvrtcProgram prog;
   if (J.create(&prog, kJitSource, "pcpd_jit.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS)
     return fail(PCPD_ECUDA, "nvrtcCreateProgram failed");
-  char dtd[64], dtda[64];
+  char dtd[64], dtda[64], dw[32];
   snprintf(dtd, sizeof dtd, "-DPCPD_JIT_TD=0x%08xu", td);
   snprintf(dtda, sizeof dtda, "-DPCPD_JIT_TDA=0x%08xu", tda);
-  const char *opts[] = {"-arch=sm_103a", "-std=c++17", "-default-device", dtd, dtda};
-  const nvrtcResult rc = J.compile(prog, 5, opts);
+  snprintf(dw, sizeof dw, "-DPCPD_JIT_W=%u", W);
+  const char *opts[] = {"-arch=sm_103a", "-std=c++17", "-default-device", dtd, dtda, dw};
+  const nvrtcResult rc = J.compile(prog, 6, opts);
   if (rc != NVRTC_SUCCESS) {
     size_t n = 0;
     J.log_size(prog, &n);
@@ -344,7 +361,8 @@ int make_plan(pcpd_t *h, const pcpd_params *prm) {
   } else {
     h->ring = false;
     h->gpi = 1;
-    h->halo = 2u * h->tau + 4u;   // 2 sites per sub-step, + one valid site past the core (pair records)
+    // W-1 sites per sub-step, + one valid site past the core (pair records), + margin
+    h->halo = (h->W - 1u) * h->tau + h->W + 1u;
     uint32_t core;
     if (seg_override) {
       core = seg_override;
@@ -362,8 +380,9 @@ int make_plan(pcpd_t *h, const pcpd_params *prm) {
     h->n_seg = (L + core - 1) / core;
     h->tile_words = (size_t)core + 2u * h->halo;
     if (h->tile_words > avail_words) return fail(PCPD_EINVAL, "tile of %zu sites exceeds shared memory", h->tile_words);
-    if (h->n_seg < 2 || h->tile_words + 12 > L)
-      return fail(PCPD_EINVAL, "segmented plan needs >= 2 tiles each shorter than L-12 (L=%u, core=%u, halo=%u)", L, core, h->halo);
+    // a tile shorter than L - 4W sees fewer candidate windows than the ring has
+    if (h->n_seg < 2 || h->tile_words + 4u * h->W > L)
+      return fail(PCPD_EINVAL, "segmented plan needs >= 2 tiles each shorter than L-4W (L=%u, core=%u, halo=%u)", L, core, h->halo);
     h->threads = 1024;
   }
   if (prm && prm->plan_threads) {
@@ -375,7 +394,7 @@ int make_plan(pcpd_t *h, const pcpd_params *prm) {
   rc = raise_smem_limit();
   if (rc) return rc;
   int per_sm = 0;
-  CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcpdk::k_sweep_persistent<false>, (int)h->threads, h->dyn_smem));
+  CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel(false, h->W), (int)h->threads, h->dyn_smem));
   if (per_sm < 1) return fail(PCPD_EINVAL, "tile plan does not fit one CTA per SM");
   h->grid = per_sm * sms;
   h->tiles = (h->G / h->gpi) * h->n_seg;
@@ -432,6 +451,7 @@ void fill_desc(const pcpd_t *h, pcpdk::InstDesc &D, uint64_t n_begin, uint64_t n
   memset(&D, 0, sizeof D);
   D.L = h->L;
   D.K = h->K;
+  D.W = h->W;
   D.G = h->G;
   D.S = h->S;
   D.pitch = h->pitch;
@@ -488,6 +508,7 @@ int launch_sweep(pcpd_t *h, uint64_t n_end, const std::vector<uint64_t> &subs, s
     pcpdk::InstDesc &D = B.single;
     D.L = h->L;
     D.K = h->K;
+    D.W = h->W;
     D.G = h->G;
     D.S = h->S;
     D.pitch = h->pitch;
@@ -526,7 +547,7 @@ int launch_sweep(pcpd_t *h, uint64_t n_end, const std::vector<uint64_t> &subs, s
                                           (CUstream)h->stream, args, nullptr);
       if (r != CUDA_SUCCESS) return fail(PCPD_ECUDA, "launch of the runtime-compiled sweep failed (%d)", (int)r);
     } else {
-      pcpdk::k_sweep_persistent<false><<<grid, h->threads, h->dyn_smem, h->stream>>>(B);
+      sweep_kernel(false, h->W)<<<grid, h->threads, h->dyn_smem, h->stream>>>(B);
       CU(cudaGetLastError());
     }
     g_launches.fetch_add(1, std::memory_order_relaxed);
@@ -552,6 +573,11 @@ int pcpd_thresholds(double p, double d, uint64_t *t_d, uint64_t *t_da) {
 
 uint64_t pcpd_substep_of_time(uint32_t L, uint64_t t) { return L < 3 ? 0 : substep_of_time(L, t); }
 
+uint64_t pcpd_substep_of_time_n(uint32_t L, uint32_t tuple, uint64_t t) {
+  const uint32_t W = (tuple ? tuple : 2u) + 1u;
+  return (tuple == 1u || tuple > 4u || L < W) ? 0 : substep_of_time(L, t, W);
+}
+
 int pcpd_create_ex(const pcpd_params *prm, pcpd_t **out) {
   if (!prm || !out) return fail(PCPD_EINVAL, "NULL argument");
   *out = nullptr;
@@ -559,6 +585,8 @@ int pcpd_create_ex(const pcpd_params *prm, pcpd_t **out) {
   if (prm->samples == 0 || prm->samples % 32 || prm->samples > (1u << 22))
     return fail(PCPD_EINVAL, "samples must be a positive multiple of 32, at most 2^22 (samples=%u)", prm->samples);
   if (prm->init < 0 || prm->init > 2) return fail(PCPD_EINVAL, "unknown init mode %d", prm->init);
+  if (prm->tuple == 1u || prm->tuple > 4u) return fail(PCPD_EINVAL, "tuple must be 0 or 2 (PCPD), 3 (TCPD) or 4 (QCPD) (tuple=%u)", prm->tuple);
+  if (prm->L < (prm->tuple ? prm->tuple : 2u) + 1u) return fail(PCPD_EINVAL, "L=%u is shorter than one window", prm->L);
   uint64_t td, tda;
   int rc = thresholds(prm->p, prm->d, &td, &tda);
   if (rc) return rc;
@@ -573,7 +601,8 @@ int pcpd_create_ex(const pcpd_params *prm, pcpd_t **out) {
   }
   pcpd_t *h = new pcpd();
   h->L = prm->L;
-  h->K = prm->L / 3u;
+  h->W = (prm->tuple ? prm->tuple : 2u) + 1u;
+  h->K = prm->L / h->W;
   h->S = prm->samples;
   h->G = prm->samples / 32u;
   h->p = prm->p;
@@ -627,7 +656,7 @@ int pcpd_create_ex(const pcpd_params *prm, pcpd_t **out) {
   const bool want = prm->jit > 0 || (prm->jit == 0 && (uint64_t)h->G * h->L >= (1ull << 22));
   if (normal && want) {
     CUfunction fn = nullptr;
-    if (jit_function(h->T.td, h->T.tda, &fn) == PCPD_OK) {
+    if (jit_function(h->T.td, h->T.tda, h->W, &fn) == PCPD_OK) {
       int per_sm = 0, sms = 0, dev = 0;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -675,21 +704,21 @@ int pcpd_run(pcpd_t *h, uint64_t steps_mcs, const uint64_t *times, size_t n_time
   if (n_times && !times) return fail(PCPD_EINVAL, "record_times_mcs is NULL");
   const uint64_t t_end = h->t_now + steps_mcs;
   if (t_end < h->t_now) return fail(PCPD_EINVAL, "time overflow");
-  const uint64_t n_end = steps_mcs ? substep_of_time(h->L, t_end) : h->n_now;
+  const uint64_t n_end = steps_mcs ? substep_of_time(h->L, t_end, h->W) : h->n_now;
   if (n_end > 0xFFFFFFFFull) return fail(PCPD_EINVAL, "sub-step count %llu would reach 2^32", (unsigned long long)n_end);
   bool now_first = false;
   std::vector<uint64_t> subs;
   for (size_t i = 0; i < n_times; ++i) {
     const uint64_t t = times[i];
     if (i && t <= times[i - 1]) return fail(PCPD_EINVAL, "record times must be strictly increasing");
-    if (t == h->t_now && i == 0 && h->n_now == substep_of_time(h->L, t)) {
+    if (t == h->t_now && i == 0 && h->n_now == substep_of_time(h->L, t, h->W)) {
       now_first = true;
       continue;
     }
     if (t <= h->t_now || t > t_end)
       return fail(PCPD_EINVAL, "record time %llu outside (%llu, %llu]", (unsigned long long)t,
                   (unsigned long long)h->t_now, (unsigned long long)t_end);
-    subs.push_back(substep_of_time(h->L, t));
+    subs.push_back(substep_of_time(h->L, t, h->W));
   }
   const size_t slot0 = h->rec_times.size();
   int rc = ensure_records(h, slot0 + n_times);
@@ -724,7 +753,7 @@ int pcpd_run_substeps(pcpd_t *h, uint64_t n_substeps) {
   std::vector<uint64_t> none;
   int rc = launch_sweep(h, n_end, none, h->rec_times.size());
   if (rc) return rc;
-  h->t_now = time_of_substep(h->L, h->n_now);
+  h->t_now = time_of_substep(h->L, h->n_now, h->W);
   return PCPD_OK;
 }
 
@@ -817,7 +846,7 @@ int pcpd_set_lattice(pcpd_t *h, const uint32_t *host_in, uint64_t substep) {
                        cudaMemcpyHostToDevice, h->stream));
   CU(cudaStreamSynchronize(h->stream));
   h->n_now = substep;
-  h->t_now = time_of_substep(h->L, substep);
+  h->t_now = time_of_substep(h->L, substep, h->W);
   h->rec_times.clear();
   if (h->d_rec_total) CU(cudaMemsetAsync(h->d_rec_total, 0, h->rec_cap * sizeof(unsigned long long), h->stream));
   if (h->d_rec_pairs) CU(cudaMemsetAsync(h->d_rec_pairs, 0, h->rec_cap * sizeof(unsigned long long), h->stream));
@@ -940,6 +969,7 @@ extern "C" int pcpd_sweep_noalloc(uint32_t *lat_in, uint32_t *lat_out, uint32_t 
     pcpdk::InstDesc &D = B.single;
     D.L = L;
     D.K = h.K;
+    D.W = h.W;
     D.G = h.G;
     D.S = samples;
     D.pitch = L;
@@ -968,7 +998,7 @@ extern "C" int pcpd_sweep_noalloc(uint32_t *lat_in, uint32_t *lat_out, uint32_t 
     B.tile_words = (uint32_t)h.tile_words;
     B.spin_limit = kSpinLimit;
     const int grid = (int)((uint64_t)h.grid < B.n_items ? (uint64_t)h.grid : B.n_items);
-    pcpdk::k_sweep_persistent<false><<<grid, h.threads, h.dyn_smem, s>>>(B);
+    sweep_kernel(false, 3u)<<<grid, h.threads, h.dyn_smem, s>>>(B);
     CU(cudaGetLastError());
     g_launches.fetch_add(1, std::memory_order_relaxed);
     uint32_t err = 0;
@@ -1137,7 +1167,12 @@ int run_multi(cudaStream_t stream, uint32_t *d_ctl, unsigned long long **d_items
       if (rc2) return rc2;
     }
     int per_sm = 0;
-    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcpdk::k_sweep_persistent<true>, threads, dyn));
+    // one window width for the whole round when every instance shares it
+    uint32_t wfix = desc.empty() ? 3u : desc[0].W;
+    for (const pcpdk::InstDesc &dd : desc)
+      if (dd.W != wfix) wfix = 0u;
+    const SweepKernel kern = sweep_kernel(true, wfix);
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, dyn));
     if (per_sm < 1) return fail(PCPD_EINVAL, "batch plan does not fit one CTA per SM");
     const int grid = (int)std::min<uint64_t>((uint64_t)per_sm * sms, items.size());
     // capture the round, then update the cached executable graph (or instantiate it)
@@ -1146,7 +1181,7 @@ int run_multi(cudaStream_t stream, uint32_t *d_ctl, unsigned long long **d_items
     cudaMemcpyToSymbolAsync(pcpdk::c_inst, gc.h_desc, desc.size() * sizeof(pcpdk::InstDesc), 0,
                             cudaMemcpyHostToDevice, stream);
     cudaMemsetAsync(d_ctl, 0, sizeof(uint32_t), stream);   // work counter
-    pcpdk::k_sweep_persistent<true><<<grid, threads, dyn, stream>>>(B);
+    kern<<<grid, threads, dyn, stream>>>(B);
     cudaGraph_t graph = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(stream, &graph);
     if (ec != cudaSuccess) {
@@ -1245,7 +1280,7 @@ int pcpd_batch_add(pcpd_batch_t *b, const pcpd_params *prm, uint64_t steps_mcs,
   pcpd_t *h = nullptr;
   int rc = pcpd_create_ex(&p2, &h);
   if (rc) return rc;
-  const uint64_t n_end = steps_mcs ? substep_of_time(h->L, steps_mcs) : 0;
+  const uint64_t n_end = steps_mcs ? substep_of_time(h->L, steps_mcs, h->W) : 0;
   if (n_end > 0xFFFFFFFFull) {
     pcpd_destroy(h);
     return fail(PCPD_EINVAL, "sub-step count would reach 2^32");
@@ -1265,14 +1300,14 @@ int pcpd_batch_run(pcpd_batch_t *b) {
   for (size_t i = 0; i < n; ++i) {
     pcpd_t *h = b->inst[i];
     tg[i].h = h;
-    tg[i].n_end = b->steps[i] ? substep_of_time(h->L, b->steps[i]) : 0;
+    tg[i].n_end = b->steps[i] ? substep_of_time(h->L, b->steps[i], h->W) : 0;
     int rc = ensure_records(h, b->rec[i].size());
     if (rc) return rc;
     if (!b->rec[i].empty()) {
       rc = ensure_rec_sub(h, b->rec[i].size());
       if (rc) return rc;
       std::vector<uint32_t> s32;
-      for (uint64_t x : b->rec[i]) s32.push_back((uint32_t)substep_of_time(h->L, x));
+      for (uint64_t x : b->rec[i]) s32.push_back((uint32_t)substep_of_time(h->L, x, h->W));
       CU(cudaMemcpyAsync(h->d_rec_sub, s32.data(), s32.size() * 4, cudaMemcpyHostToDevice, b->stream));
       tg[i].rec_sub.assign(s32.begin(), s32.end());
     }
@@ -1428,7 +1463,7 @@ void server_loop(pcpd_server_t *sv) {
         rc = ensure_rec_sub(r->h, r->rec_times.size());
         std::vector<uint32_t> s32;
         for (uint64_t t : r->rec_times) {
-          r->rec_sub.push_back(substep_of_time(r->h->L, t));
+          r->rec_sub.push_back(substep_of_time(r->h->L, t, r->h->W));
           s32.push_back((uint32_t)r->rec_sub.back());
         }
         if (rc == PCPD_OK &&
@@ -1441,7 +1476,7 @@ void server_loop(pcpd_server_t *sv) {
         server_retire(sv, r, 0, g_err);
         continue;
       }
-      r->n_end = r->steps ? substep_of_time(r->h->L, r->steps) : 0;
+      r->n_end = r->steps ? substep_of_time(r->h->L, r->steps, r->h->W) : 0;
       std::lock_guard<std::mutex> lock(sv->mu);
       r->state = 1;
       sv->active.push_back(r);
@@ -1553,6 +1588,8 @@ int pcpd_server_submit(pcpd_server_t *sv, const pcpd_params *prm, uint64_t steps
   if (n_times && !record_times_mcs) return fail(PCPD_EINVAL, "record_times_mcs is NULL");
   if (prm->L < 3 || prm->L >= (1u << 30) || prm->samples == 0 || prm->samples % 32 || prm->samples > (1u << 22))
     return fail(PCPD_EINVAL, "bad L or samples");
+  if (prm->tuple == 1u || prm->tuple > 4u || prm->L < (prm->tuple ? prm->tuple : 2u) + 1u)
+    return fail(PCPD_EINVAL, "bad tuple size or L shorter than one window");
   uint64_t td, tda;
   int rc = thresholds(prm->p, prm->d, &td, &tda);
   if (rc) return rc;
@@ -1561,7 +1598,8 @@ int pcpd_server_submit(pcpd_server_t *sv, const pcpd_params *prm, uint64_t steps
     if (record_times_mcs[i] == 0 || record_times_mcs[i] > steps_mcs)
       return fail(PCPD_EINVAL, "record times must lie in (0, steps_mcs]");
   }
-  if (steps_mcs && substep_of_time(prm->L, steps_mcs) > 0xFFFFFFFFull) return fail(PCPD_EINVAL, "too many sub-steps");
+  if (steps_mcs && substep_of_time(prm->L, steps_mcs, (prm->tuple ? prm->tuple : 2u) + 1u) > 0xFFFFFFFFull)
+    return fail(PCPD_EINVAL, "too many sub-steps");
   std::unique_ptr<Request> r(new Request());
   r->prm = *prm;
   r->steps = steps_mcs;
@@ -1690,7 +1728,7 @@ extern "C" int pcpd_dev_timeout_test(unsigned long long spin_limit_cycles) {
       B.err = b->d_ctl + 1;
       B.tile_words = (uint32_t)h->tile_words;
       B.spin_limit = spin_limit_cycles;
-      pcpdk::k_sweep_persistent<true><<<1, 256, 4 * (h->tile_words + pcpdk::sweep_queue_words(8)), h->stream>>>(B);
+      sweep_kernel(true, 3u)<<<1, 256, 4 * (h->tile_words + pcpdk::sweep_queue_words(8)), h->stream>>>(B);
       e = cudaGetLastError();
     }
     uint32_t err = 0;
@@ -1715,7 +1753,13 @@ struct TunedPlan {
   double rate;
 };
 std::mutex g_tune_mu;
+// key: (L | (W - 3) << 30, samples) -- L < 2^30, W the window width
 std::map<std::pair<uint32_t, uint32_t>, TunedPlan> g_tune;
+
+uint32_t tune_key_L(const pcpd_params *prm) {
+  const uint32_t W = (prm->tuple ? prm->tuple : 2u) + 1u;
+  return prm->L | ((W - 3u) << 30);
+}
 bool g_tune_file_read = false;
 
 void tune_file_load() {
@@ -1774,7 +1818,7 @@ int tuned_plan(const pcpd_params *prm, pcpd_params *out) {
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     tune_file_load();
-    auto it = g_tune.find({prm->L, prm->samples});
+    auto it = g_tune.find({tune_key_L(prm), prm->samples});
     if (it != g_tune.end()) {
       *out = *prm;
       out->autotune = 0;
@@ -1796,7 +1840,8 @@ extern "C" int pcpd_autotune(const pcpd_params *prm, uint32_t trial_substeps, pc
   // the default plan tells RING from SEGMENT and gives the largest tile
   pcpd base;
   base.L = prm->L;
-  base.K = prm->L / 3u;
+  base.W = (prm->tuple ? prm->tuple : 2u) + 1u;
+  base.K = prm->L / base.W;
   base.S = prm->samples;
   base.G = prm->samples / 32u;
   if (prm->samples == 0 || prm->samples % 32 || prm->L < 3) return fail(PCPD_EINVAL, "bad L or samples");
@@ -1814,7 +1859,8 @@ extern "C" int pcpd_autotune(const pcpd_params *prm, uint32_t trial_substeps, pc
     for (uint32_t th : {512u, 1024u})
       for (uint32_t tau : {64u, 128u, 256u})
         for (uint32_t seg : {base.core, half}) {
-          if (seg + 2u * (2u * tau + 4u) + 12u > prm->L || (prm->L + seg - 1) / seg < 2) continue;
+          if (seg + 2u * ((base.W - 1u) * tau + base.W + 1u) + 4u * base.W > prm->L || (prm->L + seg - 1) / seg < 2)
+            continue;
           cands.push_back({th, seg, tau});
         }
   }
@@ -1842,8 +1888,8 @@ extern "C" int pcpd_autotune(const pcpd_params *prm, uint32_t trial_substeps, pc
   if (best_rate) *best_rate = best_r;
   std::lock_guard<std::mutex> lock(g_tune_mu);
   const TunedPlan t{win.threads, win.seg, win.tau, best_r};
-  g_tune[{prm->L, prm->samples}] = t;
-  tune_file_append(prm->L, prm->samples, t);
+  g_tune[{tune_key_L(prm), prm->samples}] = t;
+  tune_file_append(tune_key_L(prm), prm->samples, t);
   return PCPD_OK;
 }
 

@@ -42,7 +42,7 @@ struct InstDesc {
   uint32_t n_seg;            // segments per column (1 for RING)
   uint32_t n_begin, n_end;   // sub-steps of this launch
   uint32_t n_rec;            // records in (n_begin, n_end]
-  uint32_t pad_;
+  uint32_t W;                // window width: tuple size + 1 (3 PCPD, 4 TCPD, 5 QCPD)
   uint32_t *buf0, *buf1;     // state at n_begin is in buf0
   const uint32_t *rec_sub;   // [n_rec] sub-step of each record (increasing)
   unsigned long long *rec_total;  // [n_rec]
@@ -130,8 +130,9 @@ __device__ __forceinline__ bool tma_ok(const uint32_t *dst, const uint32_t *src,
   return words >= 4u && (words & 3u) == 0u && (((uintptr_t)dst | (uintptr_t)src) & 15u) == 0u;
 }
 
-// Per-item tile work (the body of the tile sweep, generalised to gpi columns).
-template <bool RING>
+// Per-item tile work (the body of the tile sweep, generalised to gpi columns), for windows
+// of W sites.
+template <bool RING, int W>
 __device__ __forceinline__ void run_item(const InstDesc &D, uint32_t *smem, uint32_t *q3,
                                          uint32_t g0, uint32_t sg, uint32_t e, uint32_t *s_phi,
                                          unsigned int *s_red, unsigned int *s_q3n) {
@@ -163,7 +164,7 @@ __device__ __forceinline__ void run_item(const InstDesc &D, uint32_t *smem, uint
   Geometry G;
   G.lo = 0;
   G.hi = tile_len;
-  G.gap = L - 3u * K;
+  G.gap = L - (uint32_t)W * K;
   const uint32_t n_cand_ring = gpi * K;
   for (uint32_t n = n_a; n < n_b; ++n) {
     const uint32_t j = (n - n_a) % kPhiChunk;
@@ -181,14 +182,14 @@ __device__ __forceinline__ void run_item(const InstDesc &D, uint32_t *smem, uint
       w_lo = base + G.lo + L - G.phi;
       if (w_lo >= L) w_lo -= L;
       if (w_lo >= L) w_lo -= L;
-      if (w_lo < 3u * K) {
-        G.k_lo = w_lo / 3u;
-        G.y_first = (int)G.lo - (int)(w_lo - 3u * G.k_lo);
+      if (w_lo < (uint32_t)W * K) {
+        G.k_lo = w_lo / (uint32_t)W;
+        G.y_first = (int)G.lo - (int)(w_lo - (uint32_t)W * G.k_lo);
       } else {
         G.k_lo = 0u;
         G.y_first = (int)G.lo + (int)(L - w_lo);
       }
-      G.n_cand = (G.hi - G.lo) / 3u + 2u;
+      G.n_cand = (G.hi - G.lo) / (uint32_t)W + 2u;
     }
     const uint32_t n_cand = RING ? n_cand_ring : G.n_cand;
 
@@ -200,8 +201,8 @@ __device__ __forceinline__ void run_item(const InstDesc &D, uint32_t *smem, uint
         col = (uint32_t)(i >= K) + (uint32_t)(i >= 2u * K) + (uint32_t)(i >= 3u * K);
         ii = i - col * K;
       }
-      uint32_t k = 0, ia = 0, ib = 0, ic = 0;
-      const bool valid = i < n_cand && candidate<RING>(G, ii, L, K, k, ia, ib, ic);
+      uint32_t k = 0, idx[W] = {};
+      const bool valid = i < n_cand && candidate<RING, W>(G, ii, L, K, k, idx);
       uint32_t *sm = smem + col * L;
       const uint32_t g = g0 + col;
       Cmp cD = cmp_init(D.T.td, D.T.td_full), cA = cmp_init(D.T.tda, D.T.tda_full);
@@ -219,7 +220,7 @@ __device__ __forceinline__ void run_item(const InstDesc &D, uint32_t *smem, uint
         PCPD_CMP_A(cA, w, 11, 31);
       }
       const bool open = cmp_open2(cD, PCPD_LO_D, 21) || cmp_open2(cA, PCPD_LO_DA, 21);
-      if (valid && !open) apply_window(sm, ia, ib, ic, O, cD.lt, cA.lt);
+      if (valid && !open) apply_window<W>(sm, idx, O, cD.lt, cA.lt);
       if (valid && open) {
         const uint32_t p3 = atomicAdd(s_q3n, 1u);
         if (p3 < (uint32_t)kQ3Cap) {
@@ -231,7 +232,7 @@ __device__ __forceinline__ void run_item(const InstDesc &D, uint32_t *smem, uint
           q3[5 * kQ3Cap + p3] = cA.eq;
         } else {  // list full: finish here
           finish_from3(k, n, g, D.rk, D.T, cD, cA);
-          apply_window(sm, ia, ib, ic, O, cD.lt, cA.lt);
+          apply_window<W>(sm, idx, O, cD.lt, cA.lt);
         }
       }
     }
@@ -251,22 +252,22 @@ __device__ __forceinline__ void run_item(const InstDesc &D, uint32_t *smem, uint
         col = (uint32_t)(i >= K) + (uint32_t)(i >= 2u * K) + (uint32_t)(i >= 3u * K);
         ii = i - col * K;
       }
-      uint32_t k = 0, ia = 0, ib = 0, ic = 0;
-      candidate<RING>(G, ii, L, K, k, ia, ib, ic);
+      uint32_t k = 0, idx[W] = {};
+      candidate<RING, W>(G, ii, L, K, k, idx);
       finish_from3(k, n, g0 + col, D.rk, D.T, cD, cA);
-      apply_window(smem + col * L, ia, ib, ic, O, cD.lt, cA.lt);
+      apply_window<W>(smem + col * L, idx, O, cD.lt, cA.lt);
     }
     if (!RING) {
       const uint32_t lo_before = G.lo;
-      if (w_lo < 3u * K) {
-        const uint32_t rem = w_lo - 3u * G.k_lo;
-        if (rem) G.lo += 3u - rem;
+      if (w_lo < (uint32_t)W * K) {
+        const uint32_t rem = w_lo - (uint32_t)W * G.k_lo;
+        if (rem) G.lo += (uint32_t)W - rem;
       }
       uint32_t w_hi = w_lo + (G.hi - 1u - lo_before);
       if (w_hi >= L) w_hi -= L;
-      if (w_hi < 3u * K) {
-        const uint32_t rem = w_hi % 3u;
-        if (rem != 2u) G.hi -= 1u + rem;
+      if (w_hi < (uint32_t)W * K) {
+        const uint32_t rem = w_hi % (uint32_t)W;
+        if (rem != (uint32_t)W - 1u) G.hi -= 1u + rem;
       }
     }
     __syncthreads();
@@ -290,7 +291,9 @@ __device__ __forceinline__ const InstDesc &descriptor<true>(const BatchParams &,
   return c_inst[i];
 }
 
-template <bool BATCH>
+// WFIX: the window width of every instance of the launch (3, 4 or 5), or 0 to read it from
+// each instance's descriptor.
+template <bool BATCH, int WFIX>
 __device__ __forceinline__ void sweep_body(const BatchParams &B) {
   extern __shared__ __align__(128) uint32_t smem[];
   __shared__ uint32_t s_phi[kPhiChunk];
@@ -419,8 +422,25 @@ __device__ __forceinline__ void sweep_body(const BatchParams &B) {
     __syncthreads();
     if (s_abort) break;   // a timed-out copy may still land in shared memory: stop here
 
-    if (ring) run_item<true>(D, smem, q3, g0, sg, e, s_phi, s_red, &s_q3n);
-    else run_item<false>(D, smem, q3, g0, sg, e, s_phi, s_red, &s_q3n);
+#ifdef PCPD_JIT_W
+    // a build specialised for one window width
+    if (ring) run_item<true, PCPD_JIT_W>(D, smem, q3, g0, sg, e, s_phi, s_red, &s_q3n);
+    else run_item<false, PCPD_JIT_W>(D, smem, q3, g0, sg, e, s_phi, s_red, &s_q3n);
+#else
+    if constexpr (WFIX != 0) {
+      if (ring) run_item<true, WFIX>(D, smem, q3, g0, sg, e, s_phi, s_red, &s_q3n);
+      else run_item<false, WFIX>(D, smem, q3, g0, sg, e, s_phi, s_red, &s_q3n);
+    } else if (D.W == 4u) {
+      if (ring) run_item<true, 4>(D, smem, q3, g0, sg, e, s_phi, s_red, &s_q3n);
+      else run_item<false, 4>(D, smem, q3, g0, sg, e, s_phi, s_red, &s_q3n);
+    } else if (D.W == 5u) {
+      if (ring) run_item<true, 5>(D, smem, q3, g0, sg, e, s_phi, s_red, &s_q3n);
+      else run_item<false, 5>(D, smem, q3, g0, sg, e, s_phi, s_red, &s_q3n);
+    } else {
+      if (ring) run_item<true, 3>(D, smem, q3, g0, sg, e, s_phi, s_red, &s_q3n);
+      else run_item<false, 3>(D, smem, q3, g0, sg, e, s_phi, s_red, &s_q3n);
+    }
+#endif
 
     // ---- store the core and publish the epoch ----
     for (uint32_t c = 0; c < gpi; ++c) {
@@ -438,9 +458,9 @@ __device__ __forceinline__ void sweep_body(const BatchParams &B) {
   // except after a timed-out wait, which ends the CTA after the error is recorded)
 }
 
-template <bool BATCH>
+template <bool BATCH, int WFIX>
 __global__ void __launch_bounds__(1024, 1) k_sweep_persistent(const BatchParams B) {
-  sweep_body<BATCH>(B);
+  sweep_body<BATCH, WFIX>(B);
 }
 
 }  // namespace pcpdk

@@ -146,7 +146,7 @@ struct Masks {
   uint32_t D, A, O;
 };
 
-// One window (a, b, c) for 32 samples (Alg. 1's tree on the bond the orientation picks,
+// One window (a, b, c) for 32 samples of the PCPD (Alg. 1's tree on the bond the orientation picks,
 // written as bit logic like Alg. 2).  Lane with o=0: bond (a,b), fission target c; o=1: bond
 // (b,c), target a.  D: swap the bond; A: clear an occupied bond; otherwise (F) fill the
 // target next to an occupied bond.
@@ -163,6 +163,35 @@ __device__ __forceinline__ void window_update(uint32_t &a, uint32_t &b, uint32_t
   a = (m.O & nt) | (~m.O & nq);
   c = (m.O & nq) | (~m.O & nt);
   b = nb;
+}
+
+// One window of W = n+1 sites for 32 samples of the n-tuple process (R14; n = 3 TCPD, 4 QCPD):
+// lane with o=0: tuple (s_0..s_{n-1}), diffusion bond (s_0, s_1), fission target s_n; o=1:
+// tuple (s_1..s_n), bond (s_1, s_2), target s_0.  D: swap the bond; A: empty a full tuple;
+// otherwise (F) fill the target next to a full tuple.  (W = 3 is window_update above.)
+template <int W>
+__device__ __forceinline__ void window_update_n(uint32_t (&s)[W], const Masks &m) {
+  constexpr int n = W - 1;
+  uint32_t mid = s[1];
+#pragma unroll
+  for (int j = 2; j < n; ++j) mid &= s[j];
+  const uint32_t occ = mid & ((m.O & s[n]) | (~m.O & s[0]));   // the tuple is full
+  const uint32_t ann = m.A & occ;
+  const uint32_t fis = occ & ~(m.D | m.A);
+  const uint32_t d0 = m.D & ~m.O, d1 = m.D & m.O;               // bond (s0,s1) / (s1,s2)
+  const uint32_t n0 = (d0 & s[1]) | (~d0 & s[0]);
+  const uint32_t n1 = (d0 & s[0]) | (d1 & s[2]) | (~m.D & s[1]);
+  const uint32_t n2 = (d1 & s[1]) | (~d1 & s[2]);
+  s[0] = n0;
+  s[1] = n1;
+  s[2] = n2;
+  // a reacting lane did not diffuse, so these act on the lane's original sites
+  s[0] &= ~(ann & ~m.O);
+#pragma unroll
+  for (int j = 1; j < n; ++j) s[j] &= ~ann;
+  s[n] &= ~(ann & m.O);
+  s[n] |= fis & ~m.O;
+  s[0] |= fis & m.O;
 }
 
 // Random phase of sub-step n for phase group h: floor(x0 * L / 2^32).
@@ -236,38 +265,41 @@ __device__ __forceinline__ void tile_count(const uint32_t *sm, uint32_t y0, uint
 }
 
 // Per-sub-step geometry of the windows a tile computes.  Candidate i is window k(i) with
-// first site at tile index y(i); RING: k = i, y = (phi + 3i) mod L; SEGMENT: k = k_lo + i (mod K)
-// and y = y_first + 3i, plus the idle gap L - 3K once k wraps from K-1 to 0.
+// first site at tile index y(i); RING: k = i, y = (phi + W*i) mod L; SEGMENT: k = k_lo + i
+// (mod K) and y = y_first + W*i, plus the idle gap L - W*K once k wraps from K-1 to 0.
 struct Geometry {
   uint32_t phi, n_cand, k_lo, gap;
   int y_first;
   uint32_t lo, hi;
 };
 
-template <bool RING>
+// Window k and the tile indexes of its W sites (RING: each reduced mod L).
+template <bool RING, int W>
 __device__ __forceinline__ bool candidate(const Geometry &G, uint32_t i, uint32_t L, uint32_t K,
-                                          uint32_t &k, uint32_t &ia, uint32_t &ib, uint32_t &ic) {
+                                          uint32_t &k, uint32_t (&idx)[W]) {
   if (i >= G.n_cand) return false;
   if (RING) {
     k = i;
-    ia = G.phi + 3u * i;
-    if (ia >= L) ia -= L;
-    ib = ia + 1u;
-    if (ib >= L) ib -= L;
-    ic = ib + 1u;
-    if (ic >= L) ic -= L;
+    uint32_t a = G.phi + (uint32_t)W * i;   // phi < L and W*i < W*K <= L
+    if (a >= L) a -= L;
+    idx[0] = a;
+#pragma unroll
+    for (int j = 1; j < W; ++j) {
+      a += 1u;
+      if (a >= L) a -= L;
+      idx[j] = a;
+    }
     return true;
   } else {
     k = G.k_lo + i;
-    int y = G.y_first + 3 * (int)i;
+    int y = G.y_first + W * (int)i;
     if (k >= K) {
       k -= K;
       y += (int)G.gap;
     }
-    if (y < (int)G.lo || y + 2 >= (int)G.hi) return false;
-    ia = (uint32_t)y;
-    ib = ia + 1u;
-    ic = ia + 2u;
+    if (y < (int)G.lo || y + (W - 1) >= (int)G.hi) return false;
+#pragma unroll
+    for (int j = 0; j < W; ++j) idx[j] = (uint32_t)(y + j);
     return true;
   }
 }
@@ -307,17 +339,22 @@ __device__ __forceinline__ void finish_from3(uint32_t k, uint32_t n, uint32_t g,
   }
 }
 
-__device__ __forceinline__ void apply_window(uint32_t *sm, uint32_t ia, uint32_t ib, uint32_t ic,
-                                             uint32_t O, uint32_t ltD, uint32_t ltA) {
+template <int W>
+__device__ __forceinline__ void apply_window(uint32_t *sm, const uint32_t (&idx)[W], uint32_t O,
+                                             uint32_t ltD, uint32_t ltA) {
   Masks m;
   m.D = ltD;
   m.A = ltA & ~ltD;   // T_D <= u < T_DA
   m.O = O;
-  uint32_t a = sm[ia], b = sm[ib], c = sm[ic];
-  window_update(a, b, c, m);
-  sm[ia] = a;
-  sm[ib] = b;
-  sm[ic] = c;
+  uint32_t s[W];
+#pragma unroll
+  for (int j = 0; j < W; ++j) s[j] = sm[idx[j]];
+  if constexpr (W == 3)
+    window_update(s[0], s[1], s[2], m);
+  else
+    window_update_n<W>(s, m);
+#pragma unroll
+  for (int j = 0; j < W; ++j) sm[idx[j]] = s[j];
 }
 
 // Initial lattice: mode 0 full, 1 empty, 2 i.i.d. Bernoulli(1/2) bits (Philox tag INIT,

@@ -33,7 +33,7 @@ class Params(C.Structure):
                 ("seed", C.c_uint64), ("init", C.c_int), ("stream", C.c_void_p),
                 ("dev_lattice", C.c_void_p), ("dev_bytes", C.c_size_t), ("per_sample", C.c_int),
                 ("plan_threads", C.c_uint32), ("plan_seg_sites", C.c_uint32), ("plan_tau", C.c_uint32),
-                ("autotune", C.c_int), ("jit", C.c_int)]
+                ("autotune", C.c_int), ("jit", C.c_int), ("tuple", C.c_uint32)]
 
 
 class PlanInfo(C.Structure):
@@ -81,6 +81,7 @@ SIGNATURES = [
     ("pcpd_kernel_launches", C.c_ulonglong, []),
     ("pcpd_thresholds", C.c_int, [C.c_double, C.c_double, _u64p, _u64p]),
     ("pcpd_substep_of_time", C.c_uint64, [C.c_uint32, C.c_uint64]),
+    ("pcpd_substep_of_time_n", C.c_uint64, [C.c_uint32, C.c_uint32, C.c_uint64]),
     ("pcpd_dev_philox", C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_size_t, C.c_void_p]),
     ("pcpd_dev_rate_masks", C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_void_p, C.c_size_t, C.c_void_p]),
     ("pcpd_dev_timeout_test", C.c_int, [C.c_ulonglong]),
@@ -149,8 +150,10 @@ def thresholds(p: float, d: float):
     return int(td.value), int(tda.value)
 
 
-def substep_of_time(L: int, t: int) -> int:
-    return int(load().pcpd_substep_of_time(L, t))
+def substep_of_time(L: int, t: int, tuple_n: int = 2) -> int:
+    if tuple_n == 2:
+        return int(load().pcpd_substep_of_time(L, t))
+    return int(load().pcpd_substep_of_time_n(L, tuple_n, t))
 
 
 def _ptr(a: np.ndarray, t):
@@ -158,12 +161,13 @@ def _ptr(a: np.ndarray, t):
 
 
 class Pcpd:
-    """One simulation handle: `samples` bit-sliced PCPD samples on a ring of L sites."""
+    """One simulation handle: `samples` bit-sliced PCPD samples on a ring of L sites
+    (tuple_n = 3 / 4: the TCPD / QCPD, reacting triplets / quadruplets)."""
 
     def __init__(self, L: int, samples: int, p: float, d: float, seed: int = 1,
                  init: int = INIT_FULL, per_sample: bool = False, stream=None,
                  dev_lattice=None, plan_threads: int = 0, plan_seg_sites: int = 0,
-                 plan_tau: int = 0, autotune: bool = False, jit: int = 0):
+                 plan_tau: int = 0, autotune: bool = False, jit: int = 0, tuple_n: int = 2):
         lib = load()
         prm = Params()
         prm.L, prm.samples, prm.p, prm.d, prm.seed, prm.init = L, samples, p, d, seed, init
@@ -171,6 +175,7 @@ class Pcpd:
         prm.plan_threads, prm.plan_seg_sites, prm.plan_tau = plan_threads, plan_seg_sites, plan_tau
         prm.autotune = 1 if autotune else 0
         prm.jit = jit
+        prm.tuple = tuple_n
         if stream is not None:
             prm.stream = C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
         self._keep = dev_lattice
@@ -182,6 +187,7 @@ class Pcpd:
         self._h = h
         self.L, self.S, self.p, self.d, self.seed = L, samples, p, d, seed
         self.G = samples // 32
+        self.tuple_n = tuple_n
 
     def close(self):
         if getattr(self, "_h", None):
@@ -287,10 +293,11 @@ class Batch:
 
     def add(self, L: int, samples: int, p: float, d: float, seed: int, steps_mcs: int,
             record_times=(), init: int = INIT_FULL, plan_threads: int = 0, plan_seg_sites: int = 0,
-            plan_tau: int = 0) -> int:
+            plan_tau: int = 0, tuple_n: int = 2) -> int:
         prm = Params()
         prm.L, prm.samples, prm.p, prm.d, prm.seed, prm.init = L, samples, p, d, seed, init
         prm.plan_threads, prm.plan_seg_sites, prm.plan_tau = plan_threads, plan_seg_sites, plan_tau
+        prm.tuple = tuple_n
         t = np.ascontiguousarray(record_times, dtype=np.uint64)
         idx = C.c_size_t()
         _check(load().pcpd_batch_add(self._h, C.byref(prm), steps_mcs, _ptr(t, C.c_uint64) if t.size else None,
@@ -348,9 +355,10 @@ class Server:
         self._meta = {}
 
     def submit(self, L: int, samples: int, p: float, d: float, seed: int, steps_mcs: int,
-               record_times=(), init: int = INIT_FULL, keep_lattice: bool = False) -> int:
+               record_times=(), init: int = INIT_FULL, keep_lattice: bool = False, tuple_n: int = 2) -> int:
         prm = Params()
         prm.L, prm.samples, prm.p, prm.d, prm.seed, prm.init = L, samples, p, d, seed, init
+        prm.tuple = tuple_n
         t = np.ascontiguousarray(record_times, dtype=np.uint64)
         rid = C.c_uint64()
         _check(load().pcpd_server_submit(self._h, C.byref(prm), steps_mcs, _ptr(t, C.c_uint64) if t.size else None,
@@ -393,10 +401,12 @@ class Server:
             pass
 
 
-def autotune(L: int, samples: int, p: float, d: float, seed: int = 1, trial_substeps: int = 0):
+def autotune(L: int, samples: int, p: float, d: float, seed: int = 1, trial_substeps: int = 0,
+             tuple_n: int = 2):
     """Fastest plan for (L, samples): dict(plan_threads, plan_seg_sites, plan_tau, rate)."""
     prm = Params()
     prm.L, prm.samples, prm.p, prm.d, prm.seed = L, samples, p, d, seed
+    prm.tuple = tuple_n
     best = Params()
     rate = C.c_double()
     _check(load().pcpd_autotune(C.byref(prm), trial_substeps, C.byref(best), C.byref(rate)))
