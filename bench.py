@@ -263,6 +263,41 @@ def stream_leg(pcpd, substeps: int = 2048):
             "hbm_gbs_algorithmic": hbm, "hbm_frac_of_measured_copy": hbm / 6787.2}
 
 
+def tuple_leg(pcpd, mcs: int = 500):
+    """The n-tuple processes (TCPD n = 3, QCPD n = 4; windows of n+1 sites) on the headline
+    lattice: L = 65536, 4096 samples, full start, d = 0.5, p = 0.15, seed 1; `mcs` MCS timed
+    after 5 MCS of warm-up, through the same engine (specialised at run time)."""
+    import torch
+    out = []
+    for n in (3, 4):
+        L, S = 65536, 4096
+        stream = torch.cuda.Stream()
+        sim = pcpd.Pcpd(L, S, 0.15, 0.5, seed=1, stream=stream, tuple_n=n)
+        sim.run(5)
+        sim.sync()
+        n0 = sim.substep
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        sim.run(mcs, [5 + mcs])
+        ev1.record(stream)
+        sim.sync()
+        ms = ev0.elapsed_time(ev1)
+        K = L // (n + 1)
+        items = (S // 32) * K * (sim.substep - n0)
+        td, tda = pcpd.thresholds(0.15, 0.5)
+        _, blocks, _, mul, logic = algorithmic_ops_per_item(td, tda)
+        logic += 2.0 * (n - 2) + 3.0 * (n - 2)          # wider tuple test and updates
+        rate = items * 32 / (ms / 1e3)
+        out.append({"tuple": n, "L": L, "samples": S, "mcs": mcs, "value": rate, "unit": UNIT, "ms": ms,
+                    "rho_end": float(sim.density()[-1]), "plan": sim.plan(),
+                    "roofline": {"bound": "alu", **pipe_roofline(items / (ms / 1e3), mul, logic,
+                                                                  torch.cuda.get_device_properties(
+                                                                      torch.cuda.current_device()).multi_processor_count,
+                                                                  2070.0)}})
+        sim.close()
+    return {"workload": "TCPD / QCPD, L=65536, 4096 samples, d=0.5, p=0.15, %d MCS" % mcs, "runs": out}
+
+
 def paper_ops_per_step_thread(m: int, n_dec: int):
     """Algorithmic integer operations per (step, thread) of the paper's scheme: Philox4x32-10
     blocks ((m + n_dec + 2)/4 mask blocks, as four steps share whole blocks, and 1/128 of a
@@ -385,6 +420,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-stream", action="store_true")
     ap.add_argument("--no-paper", action="store_true")
+    ap.add_argument("--no-tuples", action="store_true")
     ap.add_argument("--paper-only", action="store_true",
                     help="run only the paper-scheme leg (for profiling) and print its JSON")
     ap.add_argument("--paper-mcs", type=int, default=1000)
@@ -525,6 +561,7 @@ def main():
     serving = serving_leg(pcpd) if not args.no_serve else None
     streamed = stream_leg(pcpd) if not args.no_stream else None
     paper = paper_leg(pcpd, mcs=args.paper_mcs) if not args.no_paper else None
+    tuples = tuple_leg(pcpd) if not args.no_tuples else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -543,7 +580,7 @@ def main():
                            "l2": "inputs larger than L2: 3 lattices x 2 buffers x 32 MiB = 192 MiB, streamed per tile epoch",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-                "gpu_launches": launches, "batch": batch, "serving": serving, "streamed": streamed, "paper_scheme": paper,
+                "gpu_launches": launches, "batch": batch, "serving": serving, "streamed": streamed, "paper_scheme": paper, "tuples": tuples,
                 "paper_context": dict(PAPER_CONTEXT, this_run_over_paper_gpu=value / PAPER_CONTEXT["gpu_moves_per_s"])}
         print(json.dumps(line), flush=True)
     for s in sims:
