@@ -25,7 +25,7 @@ typedef long long int64_t;
 typedef unsigned long long uintptr_t;
 """
 JIT_ENTRY = """
-extern "C" __global__ void __launch_bounds__(1024, 1) pcpd_jit_sweep(const pcpdk::BatchParams B) {
+extern "C" __global__ void __launch_bounds__(pcpdk::kSweepThreads, 1) pcpd_jit_sweep(const pcpdk::BatchParams B) {
   pcpdk::sweep_body<false, PCPD_JIT_W>(B);
 }
 """

@@ -354,7 +354,7 @@ int make_plan(pcpd_t *h, const pcpd_params *prm) {
     // a RING tile keeps its columns for a long stretch of sub-steps
     h->tau = (prm && prm->plan_tau) ? prm->plan_tau : (1u << 20);
     uint32_t want = (gpi * h->K + 31u) / 32u * 32u;
-    if (want > 1024u) want = 1024u;
+    if (want > pcpdk::kSweepThreads) want = pcpdk::kSweepThreads;
     if (want < 64u) want = 64u;
     h->threads = want;
     h->tile_words = (size_t)gpi * L;
@@ -383,11 +383,11 @@ int make_plan(pcpd_t *h, const pcpd_params *prm) {
     // a tile shorter than L - 4W sees fewer candidate windows than the ring has
     if (h->n_seg < 2 || h->tile_words + 4u * h->W > L)
       return fail(PCPD_EINVAL, "segmented plan needs >= 2 tiles each shorter than L-4W (L=%u, core=%u, halo=%u)", L, core, h->halo);
-    h->threads = 1024;
+    h->threads = pcpdk::kSweepThreads;
   }
   if (prm && prm->plan_threads) {
-    if (prm->plan_threads % 32 || prm->plan_threads > 1024 || prm->plan_threads < 64)
-      return fail(PCPD_EINVAL, "plan_threads must be a multiple of 32 in [64, 1024]");
+    if (prm->plan_threads % 32 || prm->plan_threads > pcpdk::kSweepThreads || prm->plan_threads < 64)
+      return fail(PCPD_EINVAL, "plan_threads must be a multiple of 32 in [64, %u]", pcpdk::kSweepThreads);
     h->threads = prm->plan_threads;
   }
   h->dyn_smem = 4 * (h->tile_words + list_words);
@@ -1159,7 +1159,7 @@ int run_multi(cudaStream_t stream, uint32_t *d_ctl, unsigned long long **d_items
     B.err = d_ctl + 1;
     B.tile_words = (uint32_t)tile_words;
     B.spin_limit = kSpinLimit;
-    const uint32_t threads = 1024;
+    const uint32_t threads = pcpdk::kSweepThreads;
     const size_t dyn = 4 * (tile_words + pcpdk::sweep_queue_words(32));
     if (dyn + kStaticSmem > (size_t)optin) return fail(PCPD_EINVAL, "batch tile exceeds shared memory");
     {
@@ -1852,11 +1852,11 @@ extern "C" int pcpd_autotune(const pcpd_params *prm, uint32_t trial_substeps, pc
   };
   std::vector<Cand> cands;
   if (base.ring) {
-    for (uint32_t th : {256u, 512u, 1024u})
-      if (th <= 1024u && (th <= base.threads * 2u || th == 256u)) cands.push_back({th, 0u, 0u});
+    for (uint32_t th : {128u, 256u, 512u})
+      if (th <= pcpdk::kSweepThreads && (th <= base.threads * 2u || th == 128u)) cands.push_back({th, 0u, 0u});
   } else {
     const uint32_t half = ((base.core / 2u) + 3u) & ~3u;
-    for (uint32_t th : {512u, 1024u})
+    for (uint32_t th : {256u, 512u})
       for (uint32_t tau : {64u, 128u, 256u})
         for (uint32_t seg : {base.core, half}) {
           if (seg + 2u * ((base.W - 1u) * tau + base.W + 1u) + 4u * base.W > prm->L || (prm->L + seg - 1) / seg < 2)

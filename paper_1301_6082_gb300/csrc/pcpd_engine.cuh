@@ -71,6 +71,10 @@ struct BatchParams {
   unsigned long long spin_limit;     // clock cycles an item may wait for a dependency
 };
 
+// Threads per CTA of the sweep (at most): 16 warps with up to 128 registers each ran the
+// L = 65536 tiles 3-8% faster than 32 warps held to 64 registers (same bits).
+constexpr uint32_t kSweepThreads = 512;
+
 constexpr uint32_t kErrDepTimeout = 1u;
 constexpr uint32_t kErrLoadTimeout = 2u;
 
@@ -459,7 +463,7 @@ __device__ __forceinline__ void sweep_body(const BatchParams &B) {
 }
 
 template <bool BATCH, int WFIX>
-__global__ void __launch_bounds__(1024, 1) k_sweep_persistent(const BatchParams B) {
+__global__ void __launch_bounds__(kSweepThreads, 1) k_sweep_persistent(const BatchParams B) {
   sweep_body<BATCH, WFIX>(B);
 }
 

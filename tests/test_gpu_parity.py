@@ -123,7 +123,7 @@ def test_ring_small_bit_exact(P, oracle_mod, L, S, p, d, init):
     np.testing.assert_array_equal(sim.lattice(), oracle_mod.pack(st))
 
 
-@pytest.mark.parametrize("L,seg,tau,threads", [(3000, 1000, 16, 256), (4099, 1500, 37, 128), (20000, 6001, 64, 1024)])
+@pytest.mark.parametrize("L,seg,tau,threads", [(3000, 1000, 16, 256), (4099, 1500, 37, 128), (20000, 6001, 64, 512)])
 def test_segmented_plan_bit_exact_and_plan_invariant(P, oracle_mod, L, seg, tau, threads):
     # Tiles with halos (temporal blocking) and a ragged last tile give the same bits as the
     # oracle and as the whole-ring plan.
@@ -319,3 +319,42 @@ def test_plans_exist_for_every_lattice_size_near_the_shared_memory_limit(P):
             sim.sync()
             plan = sim.plan()
             assert plan["ring"] == 1 or plan["core"] + 2 * plan["halo"] <= 60000
+
+
+def test_maximum_samples_sampled_groups(P, oracle_mod):
+    """2^22 samples (the largest accepted) on a short ring: 131072 groups, whole-ring tiles."""
+    L, S, p, d, seed, n1 = 64, 1 << 22, 0.15, 0.5, 5, 10
+    sim = P.Pcpd(L, S, p, d, seed=seed, init=INIT_HALF)
+    sim.run_substeps(n1)
+    lat = sim.lattice()
+    for g in (0, 4097, (S // 32) - 1):
+        st = oracle_mod.init_state(L, 32, INIT_HALF, seed, g)
+        oracle_mod.run(st, p, d, seed, 0, n1, group0=g)
+        np.testing.assert_array_equal(lat[g], oracle_mod.pack(st)[0], err_msg=f"group {g}")
+    sim.close()
+
+
+def _popcount_total(words: np.ndarray) -> int:
+    if hasattr(np, "bitwise_count"):
+        return int(np.bitwise_count(words).sum(dtype=np.uint64))
+    lut = np.array([bin(i).count("1") for i in range(256)], dtype=np.uint8)
+    b = words.view(np.uint8).reshape(-1)
+    return int(sum(int(lut[b[i:i + (1 << 26)]].sum(dtype=np.uint64)) for i in range(0, b.size, 1 << 26)))
+
+
+def test_maximum_lattice_length_closed_forms(P):
+    """L = 2^30 - 1 (the longest accepted ring), checked by properties that hold at any size:
+    p = 1, d = 0 from full empties every window's pair in the first sub-step (N = L - 2K per
+    sample, exactly), and d = 1 conserves the particle number."""
+    L, S = (1 << 30) - 1, 32
+    K = L // 3
+    sim = P.Pcpd(L, S, 1.0, 0.0, seed=3, jit=-1)
+    sim.run_substeps(1)
+    n1 = _popcount_total(sim.lattice())
+    assert n1 == S * (L - 2 * K)
+    sim.close()
+    sim = P.Pcpd(L, S, 0.3, 1.0, seed=4, init=INIT_HALF, jit=-1)
+    n0 = _popcount_total(sim.lattice())
+    sim.run_substeps(2)
+    assert _popcount_total(sim.lattice()) == n0
+    sim.close()

@@ -64,7 +64,7 @@ def test_ring_small_bit_exact(P, oracle_mod, n, L, S, p, d, init):
 
 @pytest.mark.parametrize("n,L,seg,tau,threads,jit", [
     (3, 3000, 1000, 16, 256, -1), (3, 4099, 1500, 37, 128, 1), (4, 3001, 1000, 20, 256, -1),
-    (4, 20000, 6001, 64, 1024, 1), (3, 20000, 6000, 64, 1024, -1)])
+    (4, 20000, 6001, 64, 512, 1), (3, 20000, 6000, 64, 512, -1)])
 def test_segmented_plan_bit_exact_and_plan_invariant(P, oracle_mod, n, L, seg, tau, threads, jit):
     S, p, d, seed = 64, 0.15, 0.5, 77
     ts = [3, 17, 60]
