@@ -522,37 +522,49 @@ def main():
                 "expected_philox_blocks_per_item": [round(o[1], 3) for o in ops_item],
                 "frac_of_issue_slots": (alg_ops / (ms / 1e3)) / 1e12 / issue_peak}
 
-    # end to end through the public API with host buffers (pinned), host<->device in the region
+    # end to end through the public API with host buffers (pinned), host<->device in the region:
+    # each run on its own stream, so one run's copies overlap another run's sweep
     e2e = None
     if args.e2e_steps > 0:
         host = [torch.empty((S // 32, L), dtype=torch.int32, pin_memory=True) for _ in sims]
-        for s, hb in zip(sims, host):
-            hb.numpy().view(np.uint32)[...] = s.lattice()
-        n_before = [s.substep for s in sims]
+        streams = [torch.cuda.Stream() for _ in sims]
+        esims = [pcpd.Pcpd(L, S, p, d, seed=replica_seed(W["seed"], rank), stream=st)
+                 for (d, p), st in zip(runs, streams)]
+        for es, s, hb in zip(esims, sims, host):
+            arr = hb.numpy().view(np.uint32)
+            s.lattice(out=arr)
+            es.set_lattice(arr, s.substep)        # continue where the timed runs stopped
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         att_e2e, h2d, d2h = 0, 0, 0
         for _ in range(args.e2e_steps):
-            for s, hb, nb in zip(sims, host, n_before):
+            n0s = []
+            for es, hb in zip(esims, host):
                 arr = hb.numpy().view(np.uint32)
-                s.set_lattice(arr, s.substep)
+                es.set_lattice(arr, es.substep, wait=False)
                 h2d += arr.nbytes
-                n0 = s.substep
-                recs = [t for t in rec_all if s.time_mcs < t <= s.time_mcs + mcs]
-                s.run(mcs, recs)
-                rho = s.density()
+                n0s.append(es.substep)
+                recs = [t for t in rec_all if es.time_mcs < t <= es.time_mcs + mcs]
+                es.run(mcs, recs)
+            for es, hb in zip(esims, host):
+                es.lattice(out=hb.numpy().view(np.uint32), wait=False)
+                d2h += hb.numel() * 4
+            for es, n0 in zip(esims, n0s):
+                es.sync()
+                rho = es.density()
                 d2h += rho.nbytes
-                arr[...] = s.lattice()
-                d2h += arr.nbytes
-                att_e2e += S * K_win * (s.substep - n0)
+                att_e2e += S * K_win * (es.substep - n0)
         dt = time.perf_counter() - t0
+        for es in esims:
+            es.close()
         e2e_val = att_e2e / dt
         if dist:
             (att_all,), (dt_max,) = combine(dist, [att_e2e], [dt], device="cuda")
             e2e_val = att_all / dt_max
         e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d // args.e2e_steps,
                "d2h_bytes_per_step": d2h // args.e2e_steps,
-               "note": "pcpd_set_lattice from pinned host memory + pcpd_run + pcpd_density + pcpd_get_lattice per run per step"}
+               "note": "per run per step, each run on its own stream: pcpd_set_lattice_async from pinned host "
+                       "memory, pcpd_run, pcpd_get_lattice_async into pinned memory, pcpd_sync, pcpd_density"}
 
     for s in sims:
         s.close()

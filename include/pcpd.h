@@ -123,6 +123,13 @@ int pcpd_get_lattice(const pcpd_t *h, uint32_t *host_out);
  * Resuming from a saved (lattice, sub-step) pair reproduces the uninterrupted run exactly. */
 int pcpd_set_lattice(pcpd_t *h, const uint32_t *host_in, uint64_t substep);
 
+/* The same two copies enqueued on the handle's stream without waiting: the host buffer must
+ * stay valid (and unchanged, for set) until the stream has passed the copy (pcpd_sync, or any
+ * call that waits).  With page-locked host memory the copies overlap other work on the GPU.
+ * pcpd_get_lattice_async reports an engine time-out only at the next waiting call. */
+int pcpd_get_lattice_async(const pcpd_t *h, uint32_t *host_out);
+int pcpd_set_lattice_async(pcpd_t *h, const uint32_t *host_in, uint64_t substep);
+
 /* Advance by exactly n_substeps sub-steps with no records (splice tests, fine control). */
 int pcpd_run_substeps(pcpd_t *h, uint64_t n_substeps);
 

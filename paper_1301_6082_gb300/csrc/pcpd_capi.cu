@@ -831,20 +831,23 @@ int pcpd_sample_counts(const pcpd_t *h, size_t r, uint32_t *out) {
   return PCPD_OK;
 }
 
-int pcpd_get_lattice(const pcpd_t *h, uint32_t *host_out) {
+namespace {
+
+int get_lattice(const pcpd_t *h, uint32_t *host_out, bool wait) {
   if (!h || !host_out) return fail(PCPD_EINVAL, "NULL argument");
   CU(cudaMemcpy2DAsync(host_out, (size_t)h->L * 4, h->buf[h->cur], (size_t)h->pitch * 4, (size_t)h->L * 4, h->G,
                        cudaMemcpyDeviceToHost, h->stream));
+  if (!wait) return PCPD_OK;
   CU(cudaStreamSynchronize(h->stream));
   return check_engine(h);
 }
 
-int pcpd_set_lattice(pcpd_t *h, const uint32_t *host_in, uint64_t substep) {
+int set_lattice(pcpd_t *h, const uint32_t *host_in, uint64_t substep, bool wait) {
   if (!h || !host_in) return fail(PCPD_EINVAL, "NULL argument");
   if (substep > 0xFFFFFFFFull) return fail(PCPD_EINVAL, "sub-step must be < 2^32");
   CU(cudaMemcpy2DAsync(h->buf[h->cur], (size_t)h->pitch * 4, host_in, (size_t)h->L * 4, (size_t)h->L * 4, h->G,
                        cudaMemcpyHostToDevice, h->stream));
-  CU(cudaStreamSynchronize(h->stream));
+  if (wait) CU(cudaStreamSynchronize(h->stream));
   h->n_now = substep;
   h->t_now = time_of_substep(h->L, substep, h->W);
   h->rec_times.clear();
@@ -852,6 +855,20 @@ int pcpd_set_lattice(pcpd_t *h, const uint32_t *host_in, uint64_t substep) {
   if (h->d_rec_pairs) CU(cudaMemsetAsync(h->d_rec_pairs, 0, h->rec_cap * sizeof(unsigned long long), h->stream));
   if (h->d_rec_sample) CU(cudaMemsetAsync(h->d_rec_sample, 0, h->rec_cap * (size_t)h->S * 4, h->stream));
   return PCPD_OK;
+}
+
+}  // namespace
+
+int pcpd_get_lattice(const pcpd_t *h, uint32_t *host_out) { return get_lattice(h, host_out, true); }
+
+int pcpd_get_lattice_async(const pcpd_t *h, uint32_t *host_out) { return get_lattice(h, host_out, false); }
+
+int pcpd_set_lattice(pcpd_t *h, const uint32_t *host_in, uint64_t substep) {
+  return set_lattice(h, host_in, substep, true);
+}
+
+int pcpd_set_lattice_async(pcpd_t *h, const uint32_t *host_in, uint64_t substep) {
+  return set_lattice(h, host_in, substep, false);
 }
 
 int pcpd_dev_philox(const uint32_t *ctr, uint64_t seed, uint32_t *out, size_t n, void *stream) {

@@ -72,6 +72,8 @@ SIGNATURES = [
     ("pcpd_pair_counts", C.c_int, [C.c_void_p, _u64p, C.c_size_t]),
     ("pcpd_get_lattice", C.c_int, [C.c_void_p, _u32p]),
     ("pcpd_set_lattice", C.c_int, [C.c_void_p, _u32p, C.c_uint64]),
+    ("pcpd_get_lattice_async", C.c_int, [C.c_void_p, _u32p]),
+    ("pcpd_set_lattice_async", C.c_int, [C.c_void_p, _u32p, C.c_uint64]),
     ("pcpd_run_substeps", C.c_int, [C.c_void_p, C.c_uint64]),
     ("pcpd_substep", C.c_uint64, [C.c_void_p]),
     ("pcpd_time_mcs", C.c_uint64, [C.c_void_p]),
@@ -262,15 +264,28 @@ class Pcpd:
         _check(load().pcpd_sample_counts(self._h, r, _ptr(out, C.c_uint32)))
         return out
 
-    def lattice(self) -> np.ndarray:
-        out = np.zeros((self.G, self.L), dtype=np.uint32)
-        _check(load().pcpd_get_lattice(self._h, _ptr(out, C.c_uint32)))
+    def lattice(self, out: np.ndarray | None = None, wait: bool = True) -> np.ndarray:
+        """Copy the lattice ([G][L] uint32) into `out` (a new array if None).  wait=False
+        enqueues the copy on the handle's stream (keep `out` alive, ideally page-locked, and
+        call sync() before reading it)."""
+        if out is None:
+            out = np.zeros((self.G, self.L), dtype=np.uint32)
+        assert out.dtype == np.uint32 and out.shape == (self.G, self.L) and out.flags.c_contiguous
+        fn = load().pcpd_get_lattice if wait else load().pcpd_get_lattice_async
+        _check(fn(self._h, _ptr(out, C.c_uint32)))
         return out
 
-    def set_lattice(self, words: np.ndarray, substep: int):
-        w = np.ascontiguousarray(words, dtype=np.uint32)
+    def set_lattice(self, words: np.ndarray, substep: int, wait: bool = True):
+        """Replace the lattice; wait=False enqueues the copy (`words` must be a C-contiguous
+        uint32 [G][L] array that stays unchanged until the stream has passed the copy)."""
+        if wait:
+            w = np.ascontiguousarray(words, dtype=np.uint32)
+        else:
+            w = words
+            assert w.dtype == np.uint32 and w.flags.c_contiguous
         assert w.shape == (self.G, self.L)
-        _check(load().pcpd_set_lattice(self._h, _ptr(w, C.c_uint32), substep))
+        fn = load().pcpd_set_lattice if wait else load().pcpd_set_lattice_async
+        _check(fn(self._h, _ptr(w, C.c_uint32), substep))
 
     def sync(self):
         _check(load().pcpd_sync(self._h))

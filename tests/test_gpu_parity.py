@@ -358,3 +358,22 @@ def test_maximum_lattice_length_closed_forms(P):
     sim.run_substeps(2)
     assert _popcount_total(sim.lattice()) == n0
     sim.close()
+
+
+def test_async_lattice_copies_match_waiting_ones(P):
+    import torch
+    L, S = 5000, 64
+    a = P.Pcpd(L, S, 0.2, 0.4, seed=12, init=INIT_HALF)
+    a.run(7)
+    start, n = a.lattice(), a.substep
+    a.run(9)
+    want = a.lattice()
+    pinned = torch.empty((S // 32, L), dtype=torch.int32, pin_memory=True)
+    buf = pinned.numpy().view(np.uint32)
+    buf[...] = start
+    b = P.Pcpd(L, S, 0.2, 0.4, seed=12, init=INIT_EMPTY, stream=torch.cuda.Stream())
+    b.set_lattice(buf, n, wait=False)
+    b.run(9)
+    b.lattice(out=buf, wait=False)
+    b.sync()
+    np.testing.assert_array_equal(buf, want)
