@@ -451,10 +451,12 @@ def main():
     K_win = L // 3
     runs = W["runs"]
     rec_all = log_times(W["mcs"], W["n_rec"])
-    stream = torch.cuda.Stream()
+    # the three runs are independent: one stream each, so one launch's tail overlaps the next
+    streams = [torch.cuda.Stream() for _ in runs]
+    main_stream = torch.cuda.Stream()
     sims = []
     for i, (d, p) in enumerate(runs):
-        sims.append(pcpd.Pcpd(L, S, p, d, seed=replica_seed(W["seed"], rank), stream=stream))
+        sims.append(pcpd.Pcpd(L, S, p, d, seed=replica_seed(W["seed"], rank), stream=streams[i]))
     ops_item = []
     for d, p in runs:
         td, tda = pcpd.thresholds(p, d)
@@ -480,11 +482,17 @@ def main():
     clocks.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
-    ev0.record(stream)
+    ev0.record(main_stream)
+    for st in streams:
+        st.wait_event(ev0)
     for _ in range(args.steps):
         step(sims, t_now)
         t_now += mcs
-    ev1.record(stream)
+    for st in streams:            # the end event waits for every run's stream
+        done = torch.cuda.Event()
+        done.record(st)
+        main_stream.wait_event(done)
+    ev1.record(main_stream)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
