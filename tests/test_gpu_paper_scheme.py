@@ -161,3 +161,45 @@ def test_paper_scheme_bad_args(P):
         assert h.num_records == 4 and h.step == 15
         c = h.counts()
         assert c[1] == c[2]
+
+
+def test_paper_scheme_near_the_step_counter_limit(P, oracle_mod):
+    """Steps just below 2^32: the stream block index n_w*t/4 passes 2^32 and its high bits go to
+    the counter's tag word; the run must end exactly at 2^32 - 1 and be refused beyond."""
+    n_loc, S_w, systems = 5, 64, 2
+    step0 = (1 << 32) - 1 - 77
+    rng = np.random.default_rng(8)
+    st = (rng.random((systems, 32 * n_loc * S_w)) < 0.6).astype(np.uint8)
+    with P.PaperScheme(n_loc, S_w, systems, 0.15, 0.5, 1, 2, seed=99) as h:
+        h.set_lattice(sites_to_words(st, n_loc, S_w), step0)
+        h.run(77, [step0, step0 + 40, step0 + 77])
+        got = h.counts()
+        lat = words_to_sites(h.lattice(), n_loc, S_w)
+        with pytest.raises(P.PcpdError):
+            h.run(1)
+    ref = st.copy()
+    want = oracle_mod.paper_run(ref, n_loc, S_w, 0.15, 0.5, 1, 2, 99, step0, step0 + 77,
+                                [step0, step0 + 40, step0 + 77])
+    np.testing.assert_array_equal(got, want)
+    np.testing.assert_array_equal(lat, ref)
+
+
+def test_paper_scheme_largest_system_that_fits_shared_memory(P, oracle_mod):
+    """The longest ring one CTA can hold (n_loc*S_w words up to the shared-memory limit), one
+    sampled system against the oracle; one more local word per thread is refused."""
+    import torch
+    optin = getattr(torch.cuda.get_device_properties(0), "shared_memory_per_block_optin", 232448)
+    S_w = 64
+    n_loc = optin // (4 * S_w)
+    systems, steps = 3, 3 * n_loc
+    with P.PaperScheme(n_loc, S_w, systems, 0.15, 0.5, 1, 2, seed=4) as h:
+        h.run(steps, [steps])
+        got = h.counts(per_system=True)[1]
+        lat = h.lattice()
+    for s in (0, 2):
+        ref = np.ones((1, 32 * n_loc * S_w), np.uint8)
+        want = oracle_mod.paper_run(ref, n_loc, S_w, 0.15, 0.5, 1, 2, 4, 0, steps, [steps], sys0=s)
+        assert int(got[0, s]) == int(want[0])
+        np.testing.assert_array_equal(words_to_sites(lat[s:s + 1], n_loc, S_w), ref)
+    with pytest.raises(P.PcpdError):
+        P.PaperScheme(n_loc + 1, S_w, 1, 0.15, 0.5)
