@@ -88,6 +88,14 @@ def pipe_roofline(items_per_s: float, mul_per_item: float, logic_per_item: float
             "frac_wide_multiply_pipe": f_mul}
 
 
+def measured_peak(key: str, default: float) -> float:
+    """A figure from MEASURED_PEAKS.json (the measured copy bandwidth, clocks), else default."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))[key])
+    except Exception:
+        return default
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle samples during the timed region."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -260,7 +268,7 @@ def stream_leg(pcpd, substeps: int = 2048):
     sim.close()
     return {"workload": "L=2^22, 1024 samples, d=0.5, p=0.15, %d sub-steps" % substeps,
             "value": S * (L // 3) * substeps / (ms / 1e3), "unit": UNIT, "plan": plan,
-            "hbm_gbs_algorithmic": hbm, "hbm_frac_of_measured_copy": hbm / 6787.2}
+            "hbm_gbs_algorithmic": hbm, "hbm_frac_of_measured_copy": hbm / measured_peak("hbm_gbs", 6787.2)}
 
 
 def tuple_leg(pcpd, mcs: int = 500):
