@@ -152,6 +152,8 @@ __device__ __forceinline__ void run_item(const InstDesc &D, uint32_t *smem, uint
   // the epoch's end in 64 bits: n_a + tau may pass 2^32 near the end of the counter range
   const uint32_t n_b = (uint32_t)min((unsigned long long)n_a + D.tau, (unsigned long long)D.n_end);
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  // the round keys in registers: a batch descriptor sits at a run-time index of a constant table
+  const RoundKeys rk = D.rk;
 
   // first record after n_a
   uint32_t r = 0;
@@ -215,9 +217,9 @@ __device__ __forceinline__ void run_item(const InstDesc &D, uint32_t *smem, uint
         uint32_t x0 = k, x1 = n, x2 = g, x3 = kTagDyn << 28;
         uint32_t y0 = k, y1 = n, y2 = g, y3 = (kTagDyn << 28) | 1u;
         uint32_t z0 = k, z1 = n, z2 = g, z3 = (kTagDyn << 28) | 2u;
-        philox4x32_10_rk(x0, x1, x2, x3, D.rk);
-        philox4x32_10_rk(y0, y1, y2, y3, D.rk);
-        philox4x32_10_rk(z0, z1, z2, z3, D.rk);
+        philox4x32_10_rk(x0, x1, x2, x3, rk);
+        philox4x32_10_rk(y0, y1, y2, y3, rk);
+        philox4x32_10_rk(z0, z1, z2, z3, rk);
         O = x0;
         const uint32_t w[11] = {x1, x2, x3, y0, y1, y2, y3, z0, z1, z2, z3};   // planes 31..21
         PCPD_CMP_D(cD, w, 11, 31);
@@ -235,7 +237,7 @@ __device__ __forceinline__ void run_item(const InstDesc &D, uint32_t *smem, uint
           q3[4 * kQ3Cap + p3] = cA.lt;
           q3[5 * kQ3Cap + p3] = cA.eq;
         } else {  // list full: finish here
-          finish_from3(k, n, g, D.rk, D.T, cD, cA);
+          finish_from3(k, n, g, rk, D.T, cD, cA);
           apply_window<W>(sm, idx, O, cD.lt, cA.lt);
         }
       }
@@ -258,7 +260,7 @@ __device__ __forceinline__ void run_item(const InstDesc &D, uint32_t *smem, uint
       }
       uint32_t k = 0, idx[W] = {};
       candidate<RING, W>(G, ii, L, K, k, idx);
-      finish_from3(k, n, g0 + col, D.rk, D.T, cD, cA);
+      finish_from3(k, n, g0 + col, rk, D.T, cD, cA);
       apply_window<W>(smem + col * L, idx, O, cD.lt, cA.lt);
     }
     if (!RING) {
