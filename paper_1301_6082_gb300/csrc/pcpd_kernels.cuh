@@ -56,17 +56,19 @@ __host__ __device__ inline RoundKeys make_round_keys(uint32_t k0, uint32_t k1) {
   return rk;
 }
 
-// Ten Philox4x32 rounds with the keys taken from a RoundKeys table (kernel constants).
+// Ten Philox4x32 rounds with the keys taken from a RoundKeys table (kernel constants).  The
+// 64-bit products are formed as separate high and low 32-bit multiplies (same values; measured
+// slightly faster here than the wide multiply).
 __device__ __forceinline__ void philox4x32_10_rk(uint32_t &x0, uint32_t &x1, uint32_t &x2,
                                                  uint32_t &x3, const RoundKeys &rk) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    const uint64_t p0 = (uint64_t)x0 * kPhiloxM0;
-    const uint64_t p1 = (uint64_t)x2 * kPhiloxM1;
-    x0 = (uint32_t)(p1 >> 32) ^ x1 ^ rk.k0[r];
-    x1 = (uint32_t)p1;
-    x2 = (uint32_t)(p0 >> 32) ^ x3 ^ rk.k1[r];
-    x3 = (uint32_t)p0;
+    const uint32_t h0 = __umulhi(x0, kPhiloxM0), l0 = x0 * kPhiloxM0;
+    const uint32_t h1 = __umulhi(x2, kPhiloxM1), l1 = x2 * kPhiloxM1;
+    x0 = h1 ^ x1 ^ rk.k0[r];
+    x1 = l1;
+    x2 = h0 ^ x3 ^ rk.k1[r];
+    x3 = l0;
   }
 }
 

@@ -160,9 +160,12 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 6 : 1) k_paper_sweep(const
   uint32_t s0 = 0u, s1 = 0u, s2 = 0u, s3 = 0u;  // local-site words of this lane's group
   uint32_t q0 = begin >> 2;
 
-  // one group of 4 steps (4q .. 4q+3); EDGE: the group may extend past [begin, end)
-  auto group = [&](uint32_t q, auto edge) {
+  // one group of 4 steps (4q .. 4q+3); EDGE: the group may extend past [begin, end);
+  // HASREC: a record step may fall inside (else the group has no branch and the compiler can
+  // interleave its four steps)
+  auto group = [&](uint32_t q, auto edge, auto hasrec) {
     constexpr bool EDGE = decltype(edge)::value;
+    constexpr bool HASREC = decltype(hasrec)::value;
     const uint32_t qi = (q - q0) & 31u;
     if (qi == 0u) {
       // lane i draws the local sites of the 4 steps of group q + i
@@ -200,7 +203,7 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 6 : 1) k_paper_sweep(const
         }
       }
       if (EDGE && (st < begin || st >= end)) continue;
-      if (st == next_rec) {
+      if (HASREC && st == next_rec) {
         paper_record(P, lat, w, sys, r);
         ++r;
         next_rec = r < P.n_rec ? (uint32_t)P.rec_step[r] : 0xFFFFFFFFu;
@@ -229,10 +232,13 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 6 : 1) k_paper_sweep(const
     const uint32_t q1 = (end - 1u) >> 2;
     const bool head = (begin & 3u) != 0u || q0 == q1;
     uint32_t q = q0;
-    if (head) group(q++, PaperEdge<true>{});
+    if (head) group(q++, PaperEdge<true>{}, PaperEdge<true>{});
     const uint32_t q_full_end = ((end & 3u) == 0u) ? q1 + 1u : q1;  // groups entirely inside
-    for (; q < q_full_end; ++q) group(q, PaperEdge<false>{});
-    if (q <= q1) group(q, PaperEdge<true>{});
+    for (; q < q_full_end; ++q) {
+      if ((next_rec >> 2) == q) group(q, PaperEdge<false>{}, PaperEdge<true>{});
+      else group(q, PaperEdge<false>{}, PaperEdge<false>{});
+    }
+    if (q <= q1) group(q, PaperEdge<true>{}, PaperEdge<true>{});
   }
   if (r < P.n_rec && P.rec_step[r] == (unsigned long long)end) paper_record(P, lat, w, sys, r);
   for (uint32_t i = w; i < words; i += S_w) __stcg(glat + i, lat[i]);
