@@ -34,7 +34,7 @@ from paper_1301_6082_gb300.workloads import SMEM_L65536, batch_instances, log_ti
 METRIC = "attempted site updates/s"
 # dram__bytes_read.sum + dram__bytes_write.sum of one bench-size launch of the specialised
 # sweep (one run advanced 2000 MCS), 1-pass ncu capture (profiles/pcpd_jit_sweep_L65536_S4096.md)
-TRAFFIC_PER_LAUNCH = 37.46e6 + 764.16e6
+TRAFFIC_PER_LAUNCH = 36.61e6 + 748.18e6
 UNIT = "attempts/s"
 
 
