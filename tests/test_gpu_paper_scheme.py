@@ -203,3 +203,24 @@ def test_paper_scheme_largest_system_that_fits_shared_memory(P, oracle_mod):
         np.testing.assert_array_equal(words_to_sites(lat[s:s + 1], n_loc, S_w), ref)
     with pytest.raises(P.PcpdError):
         P.PaperScheme(n_loc + 1, S_w, 1, 0.15, 0.5)
+
+
+def test_paper_scheme_records_at_launch_boundaries(P):
+    """Runs longer than one launch (2^20 steps): a record exactly at a launch boundary is taken
+    once, and the result does not depend on where the calls split the run."""
+    n_loc, S_w, systems = 4, 32, 2
+    edge = 1 << 20
+    recs = [0, edge - 1, edge, edge + 1, edge + 100]
+    with P.PaperScheme(n_loc, S_w, systems, 0.01, 1.0, 1, 0, seed=5) as a:   # d = 1: no absorption
+        a.run(edge + 100, recs)
+        ca, la = a.counts(per_system=True), a.lattice()
+        assert a.num_records == len(recs)
+    with P.PaperScheme(n_loc, S_w, systems, 0.01, 1.0, 1, 0, seed=5) as b:
+        b.run(700001, [0])
+        b.run(edge + 100 - 700001, recs[1:])
+        cb, lb = b.counts(per_system=True), b.lattice()
+    np.testing.assert_array_equal(ca[0], cb[0])
+    np.testing.assert_array_equal(ca[1], cb[1])
+    np.testing.assert_array_equal(la, lb)
+    # d = 1 conserves particles in every system
+    assert np.all(ca[1] == ca[1][0:1, :])
