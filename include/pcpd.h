@@ -315,8 +315,12 @@ void pcpd_server_stop(pcpd_server_t *sv);
  * with T_d = d*2^m (d must be a multiple of 2^-m, Sec. 4.2); the annihilation draw ANDs
  * n_dec decorrelation words with one comparison against T_c = floor(p*2^n_dec*2^32) that is
  * shared by all 32 bits of a word (the correlated draw with decorrelation of Sec. 4.3;
- * p*2^n_dec <= 1).  Random words: Philox4x32-10 keyed by the seed, counted by
- * (w, step, system, 4<<28 | block) for the masks and (0, step, system, 5<<28) for l*. */
+ * p*2^n_dec <= 1).  Random words (Philox4x32-10 keyed by the seed): each workitem w of
+ * system s has its own stream, word k being word k mod 4 of the block counted by
+ * (w, B mod 2^32, s, 4<<28 | B>>32), B = floor(k/4); step t takes the n_w = m + n_dec + 2
+ * words n_w*t .. n_w*t + n_w - 1 (diffusion planes, decorrelation words, the broadcast word,
+ * the fission word).  l* of step t: floor(x * n_loc / 2^32), x = word t mod 4 of the block
+ * (0, floor(t/4), s, 5<<28). */
 typedef struct pcpd_paper pcpd_paper_t;
 
 typedef struct pcpd_paper_params {

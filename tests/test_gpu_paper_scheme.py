@@ -120,18 +120,20 @@ def test_paper_scheme_systems_per_cta_invariance(P):
         np.testing.assert_array_equal(lat, outs[0][1])
 
 
-def test_paper_scheme_full_size_sampled(P, oracle_mod):
-    """The bench layout (n_loc = 32, S_w = 64: L = 65536; 4096 systems, the bench launch
-    shape) from full: sampled systems against the oracle run at their system offsets."""
-    n_loc, S_w, systems, steps = 32, 64, 4096, 3200
+@pytest.mark.parametrize("n_loc,S_w,systems", [(32, 64, 4096), (32, 64, 3648), (64, 32, 3648)])
+def test_paper_scheme_full_size_sampled(P, oracle_mod, n_loc, S_w, systems):
+    """The bench layouts (L = 65536 as S_w = 64 x n_loc = 32 and S_w = 32 x n_loc = 64; 3648
+    systems as the bench runs them, and 4096) from full: sampled systems against the oracle
+    run at their system offsets."""
+    steps = 100 * n_loc
     args = (0.15, 0.5, 1, 2)
-    recs = [0, 32, 160, 320, 3200]
+    recs = [0, n_loc, 5 * n_loc, 10 * n_loc, steps]
     with P.PaperScheme(n_loc, S_w, systems, *args, seed=1) as h:
         h.run(steps, recs)
         tot, ps = h.counts(per_system=True)
         lat = h.lattice()
     assert np.array_equal(ps.sum(1, dtype=np.uint64), tot)
-    for s in (0, 1, 2047, 4095):
+    for s in (0, 1, systems // 2, systems - 1):
         ref = np.ones((1, 32 * n_loc * S_w), np.uint8)
         rt = oracle_mod.paper_run(ref, n_loc, S_w, *args, 1, 0, steps, recs, sys0=s)
         np.testing.assert_array_equal(ps[:, s], rt)
