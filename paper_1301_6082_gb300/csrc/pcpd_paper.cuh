@@ -28,9 +28,9 @@
 // across the warp (bank-conflict free, the shared-memory analogue of the paper's coalesced
 // 4*S_w-byte rows).  A thread touches another thread's column only in a step whose local
 // site is within one word of a column end (l* = 0, n_loc-2 or n_loc-1); the S_w threads of a
-// system meet at a named barrier (one warp: __syncwarp) just before and just after such a
-// step and nowhere else, so systems in one CTA run independently and most steps run without
-// a barrier.
+// system meet just before and just after such a step and nowhere else (one warp: __syncwarp;
+// a system of several warps has its CTA to itself and uses the CTA barrier, or, in CTAs of
+// more than 256 threads, a named barrier per system), so most steps run without a barrier.
 #pragma once
 #include "pcpd_kernels.cuh"
 
