@@ -12,16 +12,17 @@ from .workloads import INIT_FULL, log_times
 
 
 def p_sweep(d: float, ps, L: int, samples: int, mcs: int, n_rec: int = 60, seeds=(1,),
-            init: int = INIT_FULL):
-    """Run every (p, seed) pair for `mcs` MCS from a full lattice in one batch.  Returns a
-    dict p -> {"t", "rho", "rho_pair", "delta_eff", "delta_eff_pair"} with densities averaged
-    over the seeds (counts summed exactly before dividing)."""
+            init: int = INIT_FULL, tuple_n: int = 2):
+    """Run every (p, seed) pair for `mcs` MCS from a full lattice in one batch (tuple_n = 3 /
+    4: the TCPD / QCPD).  Returns a dict p -> {"t", "rho", "rho_pair", "delta_eff",
+    "delta_eff_pair"} with densities averaged over the seeds (counts summed exactly before
+    dividing)."""
     times = log_times(mcs, n_rec)
     b = pcpd.Batch()
     index = []
     for p in ps:
         for s in seeds:
-            index.append((p, b.add(L, samples, p, d, s, mcs, times, init=init)))
+            index.append((p, b.add(L, samples, p, d, s, mcs, times, init=init, tuple_n=tuple_n)))
     b.run()
     out = {}
     for p in ps:

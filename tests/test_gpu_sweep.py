@@ -37,3 +37,17 @@ def test_p_sweep_matches_lone_runs(P):
         assert np.all(out[p]["rho_pair"] <= out[p]["rho"])
     # more annihilation, faster decay
     assert out[0.2]["rho"][-1] < out[0.12]["rho"][-1]
+
+
+def test_p_sweep_tcpd_matches_lone_runs(P):
+    from paper_1301_6082_gb300.sweep import p_sweep
+    from paper_1301_6082_gb300.workloads import log_times
+    L, S, d, mcs = 2000, 64, 0.5, 40
+    ps, seeds = (0.02, 0.1), (5,)
+    out = p_sweep(d, ps, L, S, mcs, n_rec=8, seeds=seeds, tuple_n=3)
+    times = log_times(mcs, 8)
+    for p in ps:
+        a = P.Pcpd(L, S, p, d, seed=5, tuple_n=3)
+        a.run(mcs, times)
+        np.testing.assert_array_equal(out[p]["rho"], a.counts().astype(np.int64) / (L * S))
+        a.close()
