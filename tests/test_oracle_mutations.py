@@ -12,6 +12,7 @@ import tests.test_oracle_exact as TE
 import tests.test_oracle_invariants as TI
 import tests.test_oracle_philox as TP
 import tests.test_oracle_thresholds as TT
+import tests.test_oracle_paper_scheme as TPS
 import tests.test_oracle_tuples as TU
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -34,6 +35,11 @@ MUTANTS = {
     "tuple_annihilates_two_sites": ("for (uint32_t j = 0; j < n; ++j) row[site[first + j]] = 0;",
                                     "for (uint32_t j = 0; j < 2u; ++j) row[site[first + j]] = 0;"),
     "tuple_target_next_to_pair": ("const uint32_t target = o ? 0u : n;", "const uint32_t target = o ? 0u : 2u;"),
+    # mistakes in the paper's own scheme (R13)
+    "paper_draw_not_broadcast": ("if (dec && corr) {", "if (dec && ((words[m + n_dec] >> b) & 1u)) {"),
+    "paper_fission_always_high": ("} else if ((fis >> b) & 1u) {", "} else if (fis | 1u) {"),
+    "paper_diffusion_le": ("const int diffuse = u < t_d;", "const int diffuse = u <= t_d;"),
+    "paper_site_per_workitem": ("(uint64_t)w * n_loc + istar;", "(uint64_t)w * n_loc + (istar + w) % n_loc;"),
 }
 
 
@@ -69,6 +75,10 @@ def _pins(mod):
     for L in (4, 5, 8, 9):
         yield f"exact_chain_L{L}", (lambda L=L: TE.test_schedule_oracle_matches_exact_chain(mod, L, 0.15, 0.5))
     yield "pair_density_exact_L7", lambda: TE.test_pair_density_matches_exact_chain(mod, 7)
+    yield "paper_shared_site", lambda: TPS.test_same_local_site_in_every_workitem(mod, 4, 32)
+    yield "paper_annihilation_law", lambda: TPS.test_first_step_annihilation_law(mod, 0.15, 2)
+    yield "paper_diffusion_law", lambda: TPS.test_one_step_diffusion_law(mod, 0.25, 2)
+    yield "paper_fission_sides", lambda: TPS.test_one_step_fission_sides(mod)
     for n in (3, 4):
         yield f"tuple{n}_bookkeeping", (lambda n=n: TU.test_bookkeeping_and_d1_conservation(mod, n))
         yield f"tuple{n}_closed_form", (lambda n=n: TU.test_p1_d0_first_substep_closed_form(mod, n, 61))

@@ -80,3 +80,44 @@ def test_system_offset_and_per_system_counts(oracle_mod):
         np.testing.assert_array_equal(t1, ps[:, s])
     np.testing.assert_array_equal(ps.sum(1), tot)
     np.testing.assert_array_equal(ps[-1], st.sum(1))
+
+
+@pytest.mark.parametrize("d,m", [(0.25, 2), (0.75, 2), (0.375, 3), (0.5, 1)])
+def test_one_step_diffusion_law(oracle_mod, d, m):
+    # Alternating occupation (no two neighbours occupied): no reaction can happen, and every
+    # updated bond holds one particle, so one step moves exactly one particle per diffusing
+    # bond: the changed sites are 2 x Binomial(32*S_w*systems, d) -- the dyadic diffusion draw
+    # of m planes against T_d = d*2^m.
+    n_loc, S_w, systems = 4, 64, 64
+    L = 32 * n_loc * S_w
+    st = np.zeros((systems, L), np.uint8)
+    st[:, 0::2] = 1
+    before = st.copy()
+    oracle_mod.paper_run(st, n_loc, S_w, 0.1, d, m, 1, 17, 0, 1)
+    changed = (st != before).sum(1)
+    assert np.all(changed % 2 == 0) and np.array_equal(st.sum(1), before.sum(1))
+    swaps = changed // 2
+    n = 32 * S_w
+    assert abs(swaps.mean() - n * d) < 4 * math.sqrt(n * d * (1 - d) / systems)
+    assert abs(swaps.var(ddof=1) / (n * d * (1 - d)) - 1) < 4 * math.sqrt(2 / (systems - 1)) + 0.05
+
+
+def test_one_step_fission_sides(oracle_mod):
+    # Isolated pairs on sites 4k+1, 4k+2 (n_loc a multiple of 4, so a bond's start has the
+    # residue of l*), d = 0 and T_c = 0 (no annihilation): a system whose l* hits the pairs
+    # (l* = 1 mod 4) puts one particle on 4k or 4k+3 for every bond, left or right with
+    # probability 1/2 each; any other l* changes nothing.
+    n_loc, S_w, systems = 8, 64, 256
+    L = 32 * n_loc * S_w
+    st = np.zeros((systems, L), np.uint8)
+    st[:, 1::4] = 1
+    st[:, 2::4] = 1
+    before = st.copy()
+    oracle_mod.paper_run(st, n_loc, S_w, 0.0, 0.0, 1, 0, 23, 0, 1)
+    added = st.sum(1).astype(np.int64) - before.sum(1)
+    hit = added > 0
+    assert 0 < hit.sum() < systems
+    assert np.all(added[hit] == 32 * S_w) and np.all(added[~hit] == 0)
+    left = (st[hit][:, 0::4] == 1).sum(1)
+    n = 32 * S_w
+    assert abs(left.mean() - n / 2) < 4 * math.sqrt(n / 4 / hit.sum())
