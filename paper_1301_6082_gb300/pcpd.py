@@ -348,6 +348,12 @@ class Batch:
             load().pcpd_batch_destroy(self._h)
             self._h = None
 
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
     def __del__(self):
         try:
             self.close()
@@ -408,6 +414,12 @@ class Server:
         if getattr(self, "_h", None):
             load().pcpd_server_stop(self._h)
             self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.stop()
 
     def __del__(self):
         try:
