@@ -351,8 +351,26 @@ def paper_leg(pcpd, mcs: int = 1000, systems: int = 3648):
                     "roofline": {"bound": "alu", **pipe_roofline(step_threads, mul, logic, sm_count, 2070.0),
                                  "ops_per_step_thread": ops, "philox_blocks_per_step_thread": blocks}})
         h.close()
+    # rate against the workgroup size at the same L (the paper's performance-vs-S_w study,
+    # Sec. 5.2): S_w = 32 .. 512 threads per system, n_loc = 65536 / (32 S_w), 200 MCS each
+    by_sw = []
+    for S_w in (32, 64, 128, 256, 512):
+        n_loc = 65536 // (32 * S_w)
+        stream = torch.cuda.Stream()
+        h = pcpd.PaperScheme(n_loc, S_w, systems, 0.15, 0.5, m, n_dec, seed=1, stream=stream)
+        h.run(n_loc)
+        h.sync()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        h.run(200 * n_loc)
+        ev1.record(stream)
+        h.sync()
+        ms = ev0.elapsed_time(ev1)
+        by_sw.append({"S_w": S_w, "n_loc": n_loc, "value": systems * 65536 * 200 / (ms / 1e3),
+                      "plan": h.plan()})
+        h.close()
     return {"workload": "paper scheme, L=65536, %d systems, d=0.5 (m=1), n_dec=2, p=0.15, %d MCS"
-            % (systems, mcs), "runs": out,
+            % (systems, mcs), "runs": out, "by_workgroup_size": by_sw,
             "note": "a different Markov chain from the main path (shared local site, correlated "
                     "annihilation draws); same unit as the paper's moves/s"}
 

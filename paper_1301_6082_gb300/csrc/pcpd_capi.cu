@@ -1939,24 +1939,26 @@ using PaperKernel = void (*)(const pcpdk::PaperParams);
 template <int M>
 PaperKernel paper_kernel_m(uint32_t nd) {
   switch (nd) {
-    case 0: return pcpdk::k_paper_sweep<M, 0, 256>;
-    case 1: return pcpdk::k_paper_sweep<M, 1, 256>;
-    case 2: return pcpdk::k_paper_sweep<M, 2, 256>;
-    case 3: return pcpdk::k_paper_sweep<M, 3, 256>;
-    default: return pcpdk::k_paper_sweep<-1, 0, 256>;
+    case 0: return pcpdk::k_paper_sweep<M, 0, 256, false>;
+    case 1: return pcpdk::k_paper_sweep<M, 1, 256, false>;
+    case 2: return pcpdk::k_paper_sweep<M, 2, 256, false>;
+    case 3: return pcpdk::k_paper_sweep<M, 3, 256, false>;
+    default: return pcpdk::k_paper_sweep<-1, 0, 256, false>;
   }
 }
 
 PaperKernel paper_kernel(uint32_t m, uint32_t nd, uint32_t threads, uint32_t S_w, uint32_t spc, int generic) {
-  // the small-CTA kernels hold one system per CTA unless a system is one warp
-  if (threads > 256 || (S_w > 32 && spc > 1)) return pcpdk::k_paper_sweep<-1, 0, 1024>;
-  if (generic) return pcpdk::k_paper_sweep<-1, 0, 256>;
+  // the small-CTA kernels hold one system per CTA unless a system is one warp; several
+  // multi-warp systems per CTA need named barriers
+  if (S_w > 32 && spc > 1) return pcpdk::k_paper_sweep<-1, 0, 1024, true>;   // per-system barriers
+  if (threads > 256) return pcpdk::k_paper_sweep<-1, 0, 1024, false>;
+  if (generic) return pcpdk::k_paper_sweep<-1, 0, 256, false>;
   switch (m) {
     case 0: return paper_kernel_m<0>(nd);
     case 1: return paper_kernel_m<1>(nd);
     case 2: return paper_kernel_m<2>(nd);
     case 3: return paper_kernel_m<3>(nd);
-    default: return pcpdk::k_paper_sweep<-1, 0, 256>;
+    default: return pcpdk::k_paper_sweep<-1, 0, 256, false>;
   }
 }
 

@@ -53,15 +53,16 @@ struct PaperParams {
   uint32_t systems_total;                 // row length of rec_sys
 };
 
-// The S_w threads of one system meet.  One warp: __syncwarp.  Kernels for CTAs of up to 256
-// threads hold a single system when it spans several warps, and use the CTA barrier: a named
-// barrier with a run-time id would reserve all 16 of the CTA's hardware barriers and cap
-// residency at 4 CTAs per SM.  Larger CTAs: named barrier 1 + the system's slot.
-template <int MAXT>
+// The S_w threads of one system meet.  One warp: __syncwarp.  NAMED = false: the CTA holds a
+// single system (or systems of one warp each) and uses the CTA barrier; NAMED = true: several
+// multi-warp systems share the CTA and each uses named barrier 1 + its slot.  A named barrier
+// with a run-time id reserves all 16 of the CTA's hardware barriers (4 CTAs per SM at most),
+// so only the kernels that need it have one.
+template <bool NAMED>
 __device__ __forceinline__ void paper_barrier(uint32_t id, uint32_t nthreads) {
   if (nthreads == 32u)
     __syncwarp();
-  else if (MAXT <= 256)
+  else if (!NAMED)
     __syncthreads();
   else
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
@@ -133,7 +134,8 @@ struct PaperEdge {
 // M, ND >= 0: plane and decorrelation counts fixed at compile time (every word position in
 // a 4-step group is then a constant); M < 0: read from P.  MAXT: largest CTA the kernel
 // serves; CTAs of up to 256 threads get a register budget that keeps 6 of them per SM.
-template <int M, int ND, int MAXT>
+// NAMED: per-system named barriers (see paper_barrier).
+template <int M, int ND, int MAXT, bool NAMED>
 __global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 6 : 1) k_paper_sweep(const PaperParams P) {
   extern __shared__ uint32_t s_lat[];
   const uint32_t S_w = P.S_w, n_loc = P.n_loc;
@@ -221,9 +223,9 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 6 : 1) k_paper_sweep(const
         p[S_w] = b1;
         p[2u * S_w] = cc;
       } else {
-        paper_barrier<MAXT>(bar, S_w);
+        paper_barrier<NAMED>(bar, S_w);
         paper_step_cross(lat, n_loc, S_w, w, w_lo, rot_lo, w_hi, rot_hi, ls, D, A, fis);
-        paper_barrier<MAXT>(bar, S_w);
+        paper_barrier<NAMED>(bar, S_w);
       }
     }
   };
