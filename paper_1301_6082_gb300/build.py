@@ -72,5 +72,22 @@ def build(force: bool = False, verbose: bool = False) -> str:
     return LIB
 
 
+EXAMPLE_SRC = os.path.join(HERE, "examples", "pcpd_decay.c")
+EXAMPLE_BIN = os.path.join(HERE, "examples", "pcpd_decay")
+
+
+def build_example(force: bool = False) -> str:
+    """The plain C example program, linked against the in-tree libpcpd.so (rpath $ORIGIN)."""
+    lib = build()
+    stale = force or not os.path.exists(EXAMPLE_BIN) or any(
+        os.path.getmtime(d) > os.path.getmtime(EXAMPLE_BIN) for d in (EXAMPLE_SRC, lib))
+    if stale:
+        tmp = EXAMPLE_BIN + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-I", os.path.join(os.path.dirname(HERE), "include"),
+                               EXAMPLE_SRC, "-o", tmp, "-L", HERE, "-lpcpd", "-Wl,-rpath,$ORIGIN/..", "-lm"])
+        os.replace(tmp, EXAMPLE_BIN)
+    return EXAMPLE_BIN
+
+
 if __name__ == "__main__":
     build(force=True, verbose=True)

@@ -76,3 +76,16 @@ def test_product_does_not_import_oracle():
         for f in files:
             if f.endswith((".py", ".cu", ".cuh", ".h", ".c")):
                 assert not pat.search(open(os.path.join(dirpath, f)).read()), f
+
+
+def test_c_example_builds_and_fails_loudly_without_a_device():
+    """The plain C example links against the library; on a machine without a CUDA device it
+    reports the library's error instead of computing anything."""
+    import subprocess
+    import torch
+    from paper_1301_6082_gb300 import build as B
+    exe = B.build_example()
+    if torch.cuda.is_available():
+        return   # the GPU test covers the run itself
+    r = subprocess.run([exe, "64", "32", "0.15", "0.5"], capture_output=True, text=True)
+    assert r.returncode == 6 and "pcpd error 6" in r.stderr

@@ -377,3 +377,21 @@ def test_async_lattice_copies_match_waiting_ones(P):
     b.lattice(out=buf, wait=False)
     b.sync()
     np.testing.assert_array_equal(buf, want)
+
+
+def test_c_example_program_matches_the_binding(P):
+    """The plain C user of the C ABI (examples/pcpd_decay.c) prints the same densities as the
+    Python binding for the same run (PCPD and TCPD)."""
+    import subprocess
+    from paper_1301_6082_gb300 import build as B
+    exe = B.build_example()
+    for tup in (2, 3):
+        r = subprocess.run([exe, "3000", "64", "0.15", "0.5", str(tup), "200", "9"], capture_output=True,
+                           text=True, check=True)
+        rows = np.array([[float(x) for x in line.split()] for line in r.stdout.strip().splitlines()])
+        t = rows[:, 0].astype(np.uint64)
+        sim = P.Pcpd(3000, 64, 0.15, 0.5, seed=9, tuple_n=tup)
+        sim.run(200, t)
+        np.testing.assert_allclose(rows[:, 1], sim.density(), rtol=0, atol=1e-9)
+        np.testing.assert_allclose(rows[:, 2], sim.pair_density(), rtol=0, atol=1e-9)
+        sim.close()
