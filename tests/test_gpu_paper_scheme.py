@@ -60,6 +60,8 @@ CASES = [
     (4, 32, 3, 0.0, 0.5, 1, 0, 0, 150, False),        # p = 0: no annihilation
     (4, 1024, 1, 0.15, 0.5, 1, 2, 0, 60, False),      # S_w = 1024
     (8, 256, 3, 0.15, 0.5, 1, 2, 0, 120, False),      # one system per CTA
+    (5, 32, 3, 2.0 ** -9, 37 / 256, 8, 8, 11, 90, False),   # 8 planes, 8 decorrelation words
+    (4, 32, 2, 0.5, 1.0, 0, 1, 0, 60, False),         # m = 0: d in {0, 1}
 ]
 
 

@@ -163,3 +163,22 @@ def test_bad_tuple_arguments(P):
     with pytest.raises(P.PcpdError):
         P.Pcpd(4, 32, 0.1, 0.1, tuple_n=4)      # shorter than one window
     assert P.substep_of_time(4, 10, 4) == 0
+
+
+@pytest.mark.parametrize("n,jit", [(3, -1), (4, 1)])
+def test_many_groups_multi_column_tiles(P, oracle_mod, n, jit):
+    # 2048 groups on a short ring: tiles hold 4 whole columns each; sampled groups and their
+    # per-sample records against the oracle
+    L, S, p, d, seed = 101, 65536, 0.2, 0.4, 19
+    ts = [3, 10]
+    sim = P.Pcpd(L, S, p, d, seed=seed, init=INIT_HALF, per_sample=True, jit=jit, tuple_n=n)
+    assert sim.plan()["gpi"] == 4
+    sim.run(ts[-1], ts)
+    lat = sim.lattice()
+    ps = np.stack([sim.sample_counts(r) for r in range(len(ts))])
+    subs = [oracle_mod.substep_of_time(L, t, n) for t in ts]
+    for g in (0, 3, 5, 1030, 2047):
+        st = oracle_mod.init_state(L, 32, INIT_HALF, seed, g)
+        _, pso, _ = oracle_mod.run(st, p, d, seed, 0, subs[-1], subs, per_sample=True, group0=g, tuple_n=n)
+        np.testing.assert_array_equal(lat[g], oracle_mod.pack(st)[0], err_msg=f"group {g}")
+        np.testing.assert_array_equal(ps[:, 32 * g:32 * g + 32], pso, err_msg=f"group {g}")
