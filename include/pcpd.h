@@ -283,6 +283,11 @@ int pcpd_server_submit(pcpd_server_t *sv, const pcpd_params *prm, uint64_t steps
                        const uint64_t *record_times_mcs, size_t n_times, int keep_lattice,
                        uint64_t *id_out);
 
+/* Cancel a request.  A queued request fails at once ("cancelled"); one on the GPU fails at the
+ * end of the current round, when none of its work is in flight, and its memory goes back to
+ * the budget.  PCPD_ESTATE if it has already finished, PCPD_EINVAL for an unknown id. */
+int pcpd_server_cancel(pcpd_server_t *sv, uint64_t id);
+
 /* State of a request: 0 queued, 1 on the GPU, 2 done, 3 failed. */
 int pcpd_server_poll(pcpd_server_t *sv, uint64_t id, int *state_out);
 

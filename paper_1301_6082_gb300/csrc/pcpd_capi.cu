@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <dlfcn.h>
 #include <nvrtc.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <type_traits>
 
@@ -30,6 +31,15 @@
 #include "pcpd_paper.cuh"
 
 namespace {
+
+// NVTX range around each public call that does device work (visible in profilers' timelines;
+// free when no tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 thread_local std::string g_err;
 
@@ -700,6 +710,7 @@ void pcpd_destroy(pcpd_t *h) {
 }
 
 int pcpd_run(pcpd_t *h, uint64_t steps_mcs, const uint64_t *times, size_t n_times) {
+  NvtxRange nvtx("pcpd_run");
   if (!h) return fail(PCPD_EINVAL, "NULL handle");
   if (n_times && !times) return fail(PCPD_EINVAL, "record_times_mcs is NULL");
   const uint64_t t_end = h->t_now + steps_mcs;
@@ -747,6 +758,7 @@ int pcpd_run(pcpd_t *h, uint64_t steps_mcs, const uint64_t *times, size_t n_time
 }
 
 int pcpd_run_substeps(pcpd_t *h, uint64_t n_substeps) {
+  NvtxRange nvtx("pcpd_run_substeps");
   if (!h) return fail(PCPD_EINVAL, "NULL handle");
   const uint64_t n_end = h->n_now + n_substeps;
   if (n_end > 0xFFFFFFFFull) return fail(PCPD_EINVAL, "sub-step count would reach 2^32");
@@ -1310,6 +1322,7 @@ int pcpd_batch_add(pcpd_batch_t *b, const pcpd_params *prm, uint64_t steps_mcs,
 }
 
 int pcpd_batch_run(pcpd_batch_t *b) {
+  NvtxRange nvtx("pcpd_batch_run");
   if (!b) return fail(PCPD_EINVAL, "NULL batch");
   if (b->ran) return fail(PCPD_ESTATE, "batch already ran");
   const size_t n = b->inst.size();
@@ -1390,6 +1403,7 @@ struct Request {
   size_t bytes = 0;
   std::vector<uint64_t> counts;
   std::vector<uint32_t> lattice;
+  bool cancel = false;   // set by pcpd_server_cancel while the request is on the GPU
 };
 
 size_t request_bytes(const pcpd_params &p, size_t n_rec) {
@@ -1521,7 +1535,11 @@ void server_loop(pcpd_server_t *sv) {
       round_attempts += per_sub * (tg[i].n_end - h->n_now);
     }
     const Clock::time_point t0 = Clock::now();
-    const int rc = run_multi(sv->stream, sv->d_ctl, &sv->d_items, &sv->items_cap, tg, sv->gc);
+    int rc;
+    {
+      NvtxRange nvtx("pcpd_server_round");
+      rc = run_multi(sv->stream, sv->d_ctl, &sv->d_items, &sv->items_cap, tg, sv->gc);
+    }
     const double dt = std::chrono::duration<double>(Clock::now() - t0).count();
     {
       std::lock_guard<std::mutex> lock(sv->mu);
@@ -1540,6 +1558,16 @@ void server_loop(pcpd_server_t *sv) {
         continue;
       }
       r->rec_first += tg[i].rec_taken;
+      bool cancelled;
+      {
+        std::lock_guard<std::mutex> lock(sv->mu);
+        cancelled = r->cancel;
+        if (cancelled) sv->active.erase(std::find(sv->active.begin(), sv->active.end(), r));
+      }
+      if (cancelled) {   // between rounds: nothing of this request is in flight
+        server_retire(sv, r, 0, "cancelled");
+        continue;
+      }
       if (r->h->n_now >= r->n_end) {
         r->h->t_now = r->steps;
         r->h->rec_times = r->rec_times;
@@ -1633,6 +1661,28 @@ int pcpd_server_submit(pcpd_server_t *sv, const pcpd_params *prm, uint64_t steps
   sv->st.submitted++;
   sv->cv.notify_all();
   return PCPD_OK;
+}
+
+int pcpd_server_cancel(pcpd_server_t *sv, uint64_t id) {
+  if (!sv) return fail(PCPD_EINVAL, "NULL server");
+  std::lock_guard<std::mutex> lock(sv->mu);
+  auto it = sv->all.find(id);
+  if (it == sv->all.end()) return fail(PCPD_EINVAL, "unknown request %llu", (unsigned long long)id);
+  Request *r = it->second.get();
+  if (r->state == 0) {   // still queued: it holds no device memory
+    sv->pending.erase(std::find(sv->pending.begin(), sv->pending.end(), r));
+    r->state = 3;
+    r->err = "cancelled";
+    r->t_done = Clock::now();
+    sv->st.failed++;
+    sv->cv_done.notify_all();
+    return PCPD_OK;
+  }
+  if (r->state == 1) {   // retired by the server thread after the current round
+    r->cancel = true;
+    return PCPD_OK;
+  }
+  return fail(PCPD_ESTATE, "request %llu has already finished", (unsigned long long)id);
 }
 
 int pcpd_server_poll(pcpd_server_t *sv, uint64_t id, int *state_out) {
@@ -2107,6 +2157,7 @@ void pcpd_paper_destroy(pcpd_paper_t *h) {
 }
 
 int pcpd_paper_run(pcpd_paper_t *h, uint64_t n_steps, const uint64_t *record_steps, size_t n_rec) {
+  NvtxRange nvtx("pcpd_paper_run");
   if (!h) return fail(PCPD_EINVAL, "NULL handle");
   if (n_rec && !record_steps) return fail(PCPD_EINVAL, "record_steps is NULL");
   const uint64_t end = h->step + n_steps;

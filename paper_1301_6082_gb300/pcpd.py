@@ -100,6 +100,7 @@ SIGNATURES = [
     ("pcpd_server_submit", C.c_int, [C.c_void_p, C.POINTER(Params), C.c_uint64, _u64p, C.c_size_t, C.c_int,
                                      C.POINTER(C.c_uint64)]),
     ("pcpd_server_poll", C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(C.c_int)]),
+    ("pcpd_server_cancel", C.c_int, [C.c_void_p, C.c_uint64]),
     ("pcpd_server_result", C.c_int, [C.c_void_p, C.c_uint64, _u64p, C.c_size_t, _u32p, _f64p, _f64p]),
     ("pcpd_server_wait_idle", C.c_int, [C.c_void_p]),
     ("pcpd_server_get_stats", C.c_int, [C.c_void_p, C.POINTER(ServerStats)]),
@@ -386,6 +387,10 @@ class Server:
                                          t.size, 1 if keep_lattice else 0, C.byref(rid)))
         self._meta[int(rid.value)] = (L, samples, len(t), keep_lattice)
         return int(rid.value)
+
+    def cancel(self, rid: int):
+        """Cancel a queued or running request (it then fails with "cancelled")."""
+        _check(load().pcpd_server_cancel(self._h, rid))
 
     def poll(self, rid: int) -> int:
         st = C.c_int()

@@ -67,3 +67,36 @@ def test_server_rejects_bad_requests(P):
     c, _, _, _ = sv.result(rid)
     assert c.shape == (1,)
     sv.stop()
+
+
+def test_cancel_queued_and_running_requests(P):
+    """A queued request fails at once when cancelled; a running one at the end of its round,
+    giving its memory back; the others' results are unaffected."""
+    import time
+    from paper_1301_6082_gb300.workloads import INIT_HALF
+    sv = P.Server(hbm_budget_bytes=1 << 30, max_active=1, chunk_attempts=1 << 22)
+    long_id = sv.submit(65536, 1024, 0.15, 0.5, 3, 100000, [100000])        # many rounds
+    queued_id = sv.submit(2000, 64, 0.15, 0.5, 4, 50, [50])
+    short_id = sv.submit(3000, 64, 0.2, 0.4, 5, 30, [10, 30], init=INIT_HALF, keep_lattice=True)
+    sv.cancel(queued_id)
+    assert sv.poll(queued_id) == 3
+    for _ in range(200):                       # wait until the long request is on the GPU
+        if sv.poll(long_id) == 1:
+            break
+        time.sleep(0.01)
+    sv.cancel(long_id)
+    sv.wait_idle()
+    assert sv.poll(long_id) == 3
+    with pytest.raises(P.PcpdError) as e:
+        sv.result(long_id)
+    assert "cancelled" in str(e.value)
+    with pytest.raises(P.PcpdError):
+        sv.cancel(short_id)                    # already finished
+    c, lat, _, _ = sv.result(short_id)
+    a = P.Pcpd(3000, 64, 0.2, 0.4, seed=5, init=INIT_HALF, jit=-1)
+    a.run(30, [10, 30])
+    np.testing.assert_array_equal(c, a.counts())
+    np.testing.assert_array_equal(lat, a.lattice())
+    st = sv.stats()
+    assert st["failed"] == 2 and st["completed"] == 1 and st["mem_used_bytes"] == 0
+    sv.stop()
