@@ -163,6 +163,16 @@ void pcpd_destroy(pcpd_t *h);
 /* Message for the last error on this thread ("" if none). */
 const char *pcpd_last_error(void);
 
+/* Debug builds (libpcpd_debug.so, compiled with -DPCPD_DEBUG) check every shared- and
+ * global-memory index the kernels form; a failed check skips the access and records a code
+ * (1 window site, 2 tile load into shared memory, 3 tile load from the lattice, 4 tile store,
+ * 5 paper-scheme word, 6 record read past a tile).  pcpd_debug_check() waits for the device,
+ * returns the first recorded code (0: none; always 0 in release builds; ~0 if the device could
+ * not be read) and clears it.  pcpd_debug_build() is 1 in debug builds.  Debug builds never
+ * compile the runtime-specialised sweep. */
+int pcpd_debug_build(void);
+unsigned int pcpd_debug_check(void);
+
 /* Number of CUDA kernels this library has launched in this process so far (all handles,
  * all threads).  Lets a caller count the device work of a region. */
 unsigned long long pcpd_kernel_launches(void);

@@ -60,16 +60,22 @@ def flags(extra=()):
             "-Xcompiler", "-fPIC,-ffp-contract=off,-O2", "--shared", *extra]
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
+DEBUG_LIB = os.path.join(HERE, "libpcpd_debug.so")
+
+
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    """libpcpd.so; debug=True: libpcpd_debug.so, with every kernel index checked (-DPCPD_DEBUG)."""
     write_jit_source()
-    stale = force or not os.path.exists(LIB) or any(
-        os.path.getmtime(d) > os.path.getmtime(LIB) for d in DEPS)
+    out = DEBUG_LIB if debug else LIB
+    stale = force or not os.path.exists(out) or any(
+        os.path.getmtime(d) > os.path.getmtime(out) for d in DEPS)
     if stale:
-        tmp = LIB + ".tmp%d" % os.getpid()
-        cmd = [nvcc(), *flags(["-Xptxas", "-v"] if verbose else []), *SOURCES, "-o", tmp, "-lcudart", "-ldl"]
+        tmp = out + ".tmp%d" % os.getpid()
+        extra = (["-Xptxas", "-v"] if verbose else []) + (["-DPCPD_DEBUG"] if debug else [])
+        cmd = [nvcc(), *flags(extra), *SOURCES, "-o", tmp, "-lcudart", "-ldl"]
         subprocess.check_call(cmd)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, out)
+    return out
 
 
 EXAMPLE_SRC = os.path.join(HERE, "examples", "pcpd_decay.c")

@@ -285,6 +285,10 @@ const JitApi &jit_api() {   // call with g_jit_mu held
 // Compile (once per device, threshold pair and window width) the engine with the thresholds
 // and the window width as constants.
 int jit_function(uint32_t td, uint32_t tda, uint32_t W, CUfunction *out) {
+#ifdef PCPD_DEBUG
+  (void)td, (void)tda, (void)W, (void)out;
+  return fail(PCPD_ECUDA, "debug builds run the generic sweep only (its checks live in this library)");
+#endif
   int dev = 0;
   CU(cudaGetDevice(&dev));
   CU(cudaFree(nullptr));   // the runtime's primary context is current for the driver calls
@@ -573,6 +577,26 @@ int launch_sweep(pcpd_t *h, uint64_t n_end, const std::vector<uint64_t> &subs, s
 extern "C" {
 
 const char *pcpd_last_error(void) { return g_err.c_str(); }
+
+int pcpd_debug_build(void) {
+#ifdef PCPD_DEBUG
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+unsigned int pcpd_debug_check(void) {
+#ifdef PCPD_DEBUG
+  unsigned int v = 0, zero = 0;
+  if (cudaDeviceSynchronize() != cudaSuccess) return ~0u;
+  if (cudaMemcpyFromSymbol(&v, pcpdk::g_debug_err, sizeof v) != cudaSuccess) return ~0u;
+  if (cudaMemcpyToSymbol(pcpdk::g_debug_err, &zero, sizeof zero) != cudaSuccess) return ~0u;
+  return v;
+#else
+  return 0u;
+#endif
+}
 
 unsigned long long pcpd_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 

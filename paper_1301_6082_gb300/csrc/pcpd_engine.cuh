@@ -146,6 +146,7 @@ __device__ __forceinline__ void run_item(const InstDesc &D, uint32_t *smem, uint
   const uint32_t core_len = RING ? L : min(D.core, L - s0);
   const uint32_t H = RING ? 0u : D.halo;
   const uint32_t tile_len = core_len + 2u * H;
+  const uint32_t win_lim = RING ? L : tile_len;   // a window's sites index its column's region
   const uint32_t base = RING ? 0u : (uint32_t)(((uint64_t)s0 + L - H) % L);
   const uint32_t h = (32u * g0) / 128u;   // one phase group for all gpi columns
   const uint32_t n_a = D.n_begin + e * D.tau;   // < n_end < 2^32
@@ -226,7 +227,7 @@ __device__ __forceinline__ void run_item(const InstDesc &D, uint32_t *smem, uint
         PCPD_CMP_A(cA, w, 11, 31);
       }
       const bool open = cmp_open2(cD, PCPD_LO_D, 21) || cmp_open2(cA, PCPD_LO_DA, 21);
-      if (valid && !open) apply_window<W>(sm, idx, O, cD.lt, cA.lt);
+      if (valid && !open) apply_window<W>(sm, idx, O, cD.lt, cA.lt, win_lim);
       if (valid && open) {
         const uint32_t p3 = atomicAdd(s_q3n, 1u);
         if (p3 < (uint32_t)kQ3Cap) {
@@ -238,7 +239,7 @@ __device__ __forceinline__ void run_item(const InstDesc &D, uint32_t *smem, uint
           q3[5 * kQ3Cap + p3] = cA.eq;
         } else {  // list full: finish here
           finish_from3(k, n, g, rk, D.T, cD, cA);
-          apply_window<W>(sm, idx, O, cD.lt, cA.lt);
+          apply_window<W>(sm, idx, O, cD.lt, cA.lt, win_lim);
         }
       }
     }
@@ -261,7 +262,7 @@ __device__ __forceinline__ void run_item(const InstDesc &D, uint32_t *smem, uint
       uint32_t k = 0, idx[W] = {};
       candidate<RING, W>(G, ii, L, K, k, idx);
       finish_from3(k, n, g0 + col, rk, D.T, cD, cA);
-      apply_window<W>(smem + col * L, idx, O, cD.lt, cA.lt);
+      apply_window<W>(smem + col * L, idx, O, cD.lt, cA.lt, win_lim);
     }
     if (!RING) {
       const uint32_t lo_before = G.lo;
@@ -278,6 +279,8 @@ __device__ __forceinline__ void run_item(const InstDesc &D, uint32_t *smem, uint
     }
     __syncthreads();
     if (r < D.n_rec && D.rec_sub[r] == n + 1u) {
+      // a segment's pair record reads the site after its core: it must lie inside the tile
+      if (!RING) (void)PCPD_IN_BOUNDS(H + core_len, tile_len, kDbgRecord);
       for (uint32_t c = 0; c < gpi; ++c)
         tile_count(smem + c * L, H, H + core_len, D.rec_total, D.rec_sample, D.rec_pairs, D.S, r, g0 + c,
                    RING ? L : 0u, s_red);
@@ -381,6 +384,9 @@ __device__ __forceinline__ void sweep_body(const BatchParams &B) {
       const uint32_t len[2] = {len1, tile_len - len1};
       for (int sp = 0; sp < 2; ++sp) {
         if (len[sp] == 0u) continue;
+        if (!PCPD_IN_BOUNDS((unsigned long long)c * L + off[sp] + len[sp] - 1u, B.tile_words, kDbgLoadDst) ||
+            !PCPD_IN_BOUNDS((unsigned long long)gof[sp] + len[sp] - 1u, D.pitch, kDbgLoadSrc))
+          continue;
         if (tma_ok(sm + off[sp], col + gof[sp], len[sp])) {
           if (threadIdx.x == 0) {
             if (tma_bytes == 0u) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -402,6 +408,9 @@ __device__ __forceinline__ void sweep_body(const BatchParams &B) {
         const uint32_t len[2] = {len1, tile_len - len1};
         for (int sp = 0; sp < 2; ++sp) {
           if (len[sp] == 0u || !tma_ok(sm + off[sp], col + gof[sp], len[sp])) continue;
+          if (!PCPD_IN_BOUNDS((unsigned long long)c * L + off[sp] + len[sp] - 1u, B.tile_words, kDbgLoadDst) ||
+              !PCPD_IN_BOUNDS((unsigned long long)gof[sp] + len[sp] - 1u, D.pitch, kDbgLoadSrc))
+            continue;
           uint32_t done_w = 0;
           while (done_w < len[sp]) {   // chunks of at most 32 KB
             const uint32_t w = min(len[sp] - done_w, 8192u);
@@ -452,6 +461,9 @@ __device__ __forceinline__ void sweep_body(const BatchParams &B) {
     for (uint32_t c = 0; c < gpi; ++c) {
       uint32_t *col = dst + (size_t)(g0 + c) * D.pitch + s0;
       const uint32_t *sm = smem + c * L + H;
+      if (!PCPD_IN_BOUNDS((unsigned long long)c * L + H + core_len - 1u, B.tile_words, kDbgStore) ||
+          !PCPD_IN_BOUNDS((unsigned long long)s0 + core_len - 1u, D.pitch, kDbgStore))
+        continue;
       for (uint32_t y = threadIdx.x; y < core_len; y += blockDim.x) __stcg(col + y, sm[y]);
     }
     __syncthreads();

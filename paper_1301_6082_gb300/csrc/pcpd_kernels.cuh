@@ -16,6 +16,24 @@
 
 namespace pcpdk {
 
+// Debug builds (-DPCPD_DEBUG) check every shared- and global-memory index the kernels form;
+// a failed check records its code (the first one wins) and skips the access, and the host
+// reads the code through pcpd_debug_check().  Release builds compile the checks away.
+#ifdef PCPD_DEBUG
+__device__ unsigned int g_debug_err;
+__device__ __forceinline__ bool debug_in_bounds(unsigned long long i, unsigned long long n,
+                                                unsigned int code) {
+  if (i < n) return true;
+  atomicCAS(&g_debug_err, 0u, code);
+  return false;
+}
+#define PCPD_IN_BOUNDS(i, n, code) pcpdk::debug_in_bounds((i), (n), (code))
+#else
+#define PCPD_IN_BOUNDS(i, n, code) true
+#endif
+constexpr unsigned int kDbgWindow = 1u, kDbgLoadDst = 2u, kDbgLoadSrc = 3u, kDbgStore = 4u,
+                       kDbgPaper = 5u, kDbgRecord = 6u;
+
 constexpr uint32_t kTagDyn = 0u;
 constexpr uint32_t kTagPhase = 1u;
 constexpr uint32_t kTagInit = 2u;
@@ -343,7 +361,11 @@ __device__ __forceinline__ void finish_from3(uint32_t k, uint32_t n, uint32_t g,
 
 template <int W>
 __device__ __forceinline__ void apply_window(uint32_t *sm, const uint32_t (&idx)[W], uint32_t O,
-                                             uint32_t ltD, uint32_t ltA) {
+                                             uint32_t ltD, uint32_t ltA, uint32_t lim) {
+#pragma unroll
+  for (int j = 0; j < W; ++j)
+    if (!PCPD_IN_BOUNDS(idx[j], lim, kDbgWindow)) return;
+  (void)lim;
   Masks m;
   m.D = ltD;
   m.A = ltA & ~ltD;   // T_D <= u < T_DA

@@ -115,6 +115,11 @@ __device__ __forceinline__ void paper_step_cross(uint32_t *lat, uint32_t n_loc, 
   const uint32_t r_1 = (ls + 1u < n_loc) ? 0u : rot_hi;
   const uint32_t i_2 = (ls + 2u < n_loc) ? (ls + 2u) * S_w + w : (ls + 2u - n_loc) * S_w + w_hi;
   const uint32_t r_2 = (ls + 2u < n_loc) ? 0u : rot_hi;
+  const uint32_t words = n_loc * S_w;
+  if (!PCPD_IN_BOUNDS(i_a, words, kDbgPaper) || !PCPD_IN_BOUNDS(i_0, words, kDbgPaper) ||
+      !PCPD_IN_BOUNDS(i_1, words, kDbgPaper) || !PCPD_IN_BOUNDS(i_2, words, kDbgPaper))
+    return;
+  (void)words;
   uint32_t a = __funnelshift_l(lat[i_a], lat[i_a], r_a);
   uint32_t b0 = lat[i_0];
   uint32_t b1 = __funnelshift_r(lat[i_1], lat[i_1], r_1);
@@ -213,6 +218,7 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 6 : 1) k_paper_sweep(const
       const uint32_t x = __shfl_sync(~0u, pick4(s0, s1, s2, s3, j), qi);
       const uint32_t ls = (uint32_t)(((unsigned long long)x * n_loc) >> 32);
       const uint32_t D = P.d_full ? ~0u : lt, A = dec & corr;
+      if (!PCPD_IN_BOUNDS(ls, n_loc, kDbgPaper)) continue;
       if (ls != 0u && ls + 2u < n_loc) {
         // the common case: all four sites in the thread's own column, no rotation
         uint32_t *p = lat + ls * S_w + w;

@@ -12,7 +12,8 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libpcpd.so")
+# PCPD_LIB may name another build of the library (e.g. libpcpd_debug.so, the index-checked one)
+LIB_PATH = os.environ.get("PCPD_LIB") or os.path.join(_HERE, "libpcpd.so")
 
 PCPD_OK, PCPD_EINVAL, PCPD_ENOMEM, PCPD_ECUDA, PCPD_ETIMEOUT, PCPD_ESTATE, PCPD_ENODEV = range(7)
 INIT_FULL, INIT_EMPTY, INIT_HALF = 0, 1, 2
@@ -80,6 +81,8 @@ SIGNATURES = [
     ("pcpd_sync", C.c_int, [C.c_void_p]),
     ("pcpd_destroy", None, [C.c_void_p]),
     ("pcpd_last_error", C.c_char_p, []),
+    ("pcpd_debug_build", C.c_int, []),
+    ("pcpd_debug_check", C.c_uint, []),
     ("pcpd_kernel_launches", C.c_ulonglong, []),
     ("pcpd_thresholds", C.c_int, [C.c_double, C.c_double, _u64p, _u64p]),
     ("pcpd_substep_of_time", C.c_uint64, [C.c_uint32, C.c_uint64]),
@@ -561,3 +564,13 @@ class PaperScheme:
 
     def sync(self):
         _check(load().pcpd_paper_sync(self._h))
+
+
+def debug_build() -> bool:
+    """True when the loaded library is the index-checked debug build."""
+    return bool(load().pcpd_debug_build())
+
+
+def debug_check() -> int:
+    """First failed index check since the last call (0: none), in debug builds; 0 otherwise."""
+    return int(load().pcpd_debug_check())
