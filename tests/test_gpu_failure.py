@@ -32,3 +32,18 @@ def test_dependency_wait_times_out_and_context_survives(P):
     b = P.Pcpd(200, 32, 0.15, 0.5, seed=3)
     b.run(5, [5])
     np.testing.assert_array_equal(a.lattice(), b.lattice())
+
+
+def test_allocation_failure_is_reported_and_the_context_survives(P):
+    """An instance far larger than device memory (2^30 sites x 2^22 samples = 2^49 bytes):
+    cudaMalloc fails, the call returns PCPD_ENOMEM, and the device keeps working."""
+    with pytest.raises(P.PcpdError) as e:
+        P.Pcpd((1 << 30) - 1, 1 << 22, 0.15, 0.5)
+    assert e.value.code == P.PCPD_ENOMEM
+    with pytest.raises(P.PcpdError) as e:
+        P.PaperScheme(32, 1024, 1 << 24, 0.15, 0.5)     # 2^24 systems of 128 KiB
+    assert e.value.code == P.PCPD_ENOMEM
+    sim = P.Pcpd(1000, 64, 0.15, 0.5)
+    sim.run(5, [5])
+    assert sim.counts()[0] > 0
+    sim.close()
