@@ -411,7 +411,11 @@ int make_plan(pcpd_t *h, const pcpd_params *prm) {
   CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel(false, h->W), (int)h->threads, h->dyn_smem));
   if (per_sm < 1) return fail(PCPD_EINVAL, "tile plan does not fit one CTA per SM");
   h->grid = per_sm * sms;
-  h->tiles = (h->G / h->gpi) * h->n_seg;
+  const uint64_t tiles = (uint64_t)(h->G / h->gpi) * h->n_seg;
+  if (tiles >= (1ull << 24))   // a work item carries the tile index in 24 bits
+    return fail(PCPD_EINVAL, "%llu tiles per epoch (at most 2^24 - 1): fewer samples or longer tiles",
+                (unsigned long long)tiles);
+  h->tiles = (uint32_t)tiles;
   return PCPD_OK;
 }
 
@@ -508,7 +512,9 @@ constexpr unsigned long long kSpinLimit = 40ull * 1000 * 1000 * 1000;   // ~20 s
 // Sweep from n_now to n_end in engine launches; records subs[0..) (absolute sub-steps in
 // (n_now, n_end], already copied to d_rec_sub) go to record slots [slot0, ...).
 int launch_sweep(pcpd_t *h, uint64_t n_end, const std::vector<uint64_t> &subs, size_t slot0) {
-  const uint64_t max_epochs = 1u << 22;
+  // epochs per launch: the epoch field of a work item has 24 bits, and the launch's item
+  // count (epochs x tiles) must fit 32 bits
+  const uint64_t max_epochs = std::min<uint64_t>(1u << 22, 0xFFFFFFFFull / h->tiles);
   size_t ri = 0;
   while (h->n_now < n_end) {
     const uint64_t span = n_end - h->n_now;
@@ -1011,7 +1017,7 @@ extern "C" int pcpd_sweep_noalloc(uint32_t *lat_in, uint32_t *lat_out, uint32_t 
   int cur = 0;
   uint64_t n_now = substep_begin;
   const uint64_t n_end = substep_begin + n_substeps;
-  const uint64_t max_epochs = 1u << 22;
+  const uint64_t max_epochs = std::min<uint64_t>(1u << 22, 0xFFFFFFFFull / h.tiles);
   while (n_now < n_end) {
     const uint64_t span = n_end - n_now;
     const uint64_t epochs_all = (span + h.tau - 1) / h.tau;
@@ -1187,6 +1193,7 @@ int run_multi(cudaStream_t stream, uint32_t *d_ctl, unsigned long long **d_items
     }
     add_ring(ring_items.size());
     if (items.empty()) continue;
+    if (items.size() > 0xFFFFFFFFull) return fail(PCPD_EINVAL, "a batch round of %zu work items is too large", items.size());
     if (items.size() > *items_cap) {
       CU(cudaStreamSynchronize(stream));
       cudaFree(*d_items);

@@ -395,3 +395,10 @@ def test_c_example_program_matches_the_binding(P):
         np.testing.assert_allclose(rows[:, 1], sim.density(), rtol=0, atol=1e-9)
         np.testing.assert_allclose(rows[:, 2], sim.pair_density(), rtol=0, atol=1e-9)
         sim.close()
+
+
+def test_tile_count_limit_is_enforced(P):
+    # a work item carries its tile index in 24 bits: plans beyond 2^24 - 1 tiles are refused
+    with pytest.raises(P.PcpdError) as e:
+        P.Pcpd(1 << 22, 1 << 22, 0.1, 0.1, plan_seg_sites=1024, plan_tau=16)
+    assert e.value.code == P.PCPD_EINVAL and "tiles" in str(e.value)
