@@ -35,10 +35,11 @@ def test_dependency_wait_times_out_and_context_survives(P):
 
 
 def test_allocation_failure_is_reported_and_the_context_survives(P):
-    """An instance far larger than device memory (2^30 sites x 2^22 samples = 2^49 bytes):
-    cudaMalloc fails, the call returns PCPD_ENOMEM, and the device keeps working."""
+    """An instance far larger than device memory (2^29 sites x 2^14 samples, two buffers: 2.2 TB)
+    with a valid plan: cudaMalloc fails, the call returns PCPD_ENOMEM, and the device keeps
+    working."""
     with pytest.raises(P.PcpdError) as e:
-        P.Pcpd((1 << 30) - 1, 1 << 22, 0.15, 0.5)
+        P.Pcpd(1 << 29, 1 << 14, 0.15, 0.5)
     assert e.value.code == P.PCPD_ENOMEM
     with pytest.raises(P.PcpdError) as e:
         P.PaperScheme(32, 1024, 1 << 24, 0.15, 0.5)     # 2^24 systems of 128 KiB
