@@ -66,6 +66,31 @@ int fail(int code, const char *fmt, ...) {
 
 constexpr uint64_t kTwo32 = 4294967296ull;
 
+// Device allocation of the library's large buffers.  A request larger than the device's free
+// memory is refused up front (PCPD_ENOMEM) rather than handed to cudaMalloc.  Tests can make
+// the n-th such allocation of the process fail by setting PCPD_INJECT_ALLOC_FAILURE=n (host-
+// side fault injection: nothing is allocated and the device is not touched).
+std::atomic<long long> g_alloc_countdown{-2};   // -2: not read yet, -1: no injection
+
+int dev_alloc(void **p, size_t bytes, const char *what) {
+  long long c = g_alloc_countdown.load();
+  if (c == -2) {
+    const char *env = getenv("PCPD_INJECT_ALLOC_FAILURE");
+    long long v = env ? atoll(env) : -1;
+    g_alloc_countdown.compare_exchange_strong(c, v > 0 ? v : -1);
+  }
+  if (g_alloc_countdown.load() > 0 && --g_alloc_countdown == 0)
+    return fail(PCPD_ENOMEM, "%s: injected allocation failure (%zu bytes)", what, bytes);
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && bytes > free_b)
+    return fail(PCPD_ENOMEM, "%s: %zu bytes requested, %zu free on the device", what, bytes, free_b);
+  const cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess)
+    return fail(e == cudaErrorMemoryAllocation ? PCPD_ENOMEM : PCPD_ECUDA, "%s: cudaMalloc(%zu): %s", what, bytes,
+                cudaGetErrorString(e));
+  return PCPD_OK;
+}
+
 // Rates of Eq. (1) as integer thresholds, evaluated in double exactly as written (the
 // library is compiled with -ffp-contract=off, so no product is fused).
 uint64_t floor_scaled(double x) {
@@ -677,8 +702,8 @@ int pcpd_create_ex(const pcpd_params *prm, pcpd_t **out) {
     h->buf[0] = (uint32_t *)prm->dev_lattice;
     h->buf[1] = h->buf[0] + words;
   } else {
-    cudaError_t e = cudaMalloc(&h->buf[0], 2 * words * 4);
-    if (e != cudaSuccess) return bail(fail(PCPD_ENOMEM, "cudaMalloc(%zu): %s", 2 * words * 4, cudaGetErrorString(e)));
+    const int ra = dev_alloc((void **)&h->buf[0], 2 * words * 4, "lattice");
+    if (ra) return bail(ra);
     h->buf[1] = h->buf[0] + words;
     h->own_mem = true;
   }
@@ -2168,9 +2193,9 @@ int pcpd_paper_create(const pcpd_paper_params *prm, pcpd_paper_t **out) {
     h->own_stream = true;
   }
   const size_t bytes = (size_t)h->systems * words * 4;
-  cudaError_t e = cudaMalloc(&h->d_lat, bytes);
-  if (e != cudaSuccess) return bail(fail(PCPD_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e)));
-  e = cudaMemsetAsync(h->d_lat, prm->init == PCPD_INIT_FULL ? 0xFF : 0x00, bytes, h->stream);
+  const int ra = dev_alloc((void **)&h->d_lat, bytes, "systems");
+  if (ra) return bail(ra);
+  cudaError_t e = cudaMemsetAsync(h->d_lat, prm->init == PCPD_INIT_FULL ? 0xFF : 0x00, bytes, h->stream);
   if (e != cudaSuccess) return bail(fail(PCPD_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e)));
   *out = h;
   return PCPD_OK;

@@ -35,12 +35,11 @@ def test_dependency_wait_times_out_and_context_survives(P):
 
 
 def test_allocation_failure_is_reported_and_the_context_survives(P):
-    """An instance far larger than device memory (2^29 sites x 2^14 samples, two buffers: 2.2 TB)
-    with a valid plan: cudaMalloc fails, the call returns PCPD_ENOMEM, and the device keeps
-    working."""
+    """A lattice larger than the device's free memory (2^29 sites x 2^14 samples, two buffers:
+    2.2 TB) is refused before any allocation (PCPD_ENOMEM); the device keeps working."""
     with pytest.raises(P.PcpdError) as e:
         P.Pcpd(1 << 29, 1 << 14, 0.15, 0.5)
-    assert e.value.code == P.PCPD_ENOMEM
+    assert e.value.code == P.PCPD_ENOMEM and "free" in str(e.value)
     with pytest.raises(P.PcpdError) as e:
         P.PaperScheme(32, 1024, 1 << 24, 0.15, 0.5)     # 2^24 systems of 128 KiB
     assert e.value.code == P.PCPD_ENOMEM
@@ -48,3 +47,30 @@ def test_allocation_failure_is_reported_and_the_context_survives(P):
     sim.run(5, [5])
     assert sim.counts()[0] > 0
     sim.close()
+
+
+def test_injected_allocation_failure(P):
+    """Host-side fault injection: with PCPD_INJECT_ALLOC_FAILURE=2 the second large allocation
+    of the process fails (nothing is allocated), the call reports PCPD_ENOMEM and later calls
+    work."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = (
+        "import sys; sys.path.insert(0, sys.argv[1])\n"
+        "from paper_1301_6082_gb300 import pcpd\n"
+        "a = pcpd.Pcpd(1000, 64, 0.15, 0.5)\n"
+        "try:\n"
+        "    pcpd.Pcpd(1000, 64, 0.15, 0.5)\n"
+        "    print('no failure')\n"
+        "except pcpd.PcpdError as e:\n"
+        "    print('code', e.code, 'injected' in str(e))\n"
+        "c = pcpd.Pcpd(2000, 32, 0.2, 0.5)\n"
+        "c.run(3, [3]); a.run(3, [3])\n"
+        "print('ok', int(c.counts()[0]) > 0, int(a.counts()[0]) > 0)\n")
+    env = dict(os.environ, PCPD_INJECT_ALLOC_FAILURE="2")
+    r = subprocess.run([sys.executable, "-c", script, root], capture_output=True, text=True, env=env, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = r.stdout.strip().splitlines()
+    assert lines[-2] == "code 2 True" and lines[-1] == "ok True True", lines
