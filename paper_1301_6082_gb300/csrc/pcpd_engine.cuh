@@ -3,8 +3,11 @@
 //
 // Item = (instance, epoch e, tile).  A tile is either a group of whole columns (RING: gpi
 // 32-sample groups that fit in shared memory, updated with periodic indexing) or one
-// segment of one column with a halo of H >= 2*tau + 1 sites on each side (SEGMENT, temporal
-// blocking; the extra site keeps the one after the core valid for pair records).  Epoch e covers sub-steps [n_begin + e*tau, ... + tau).
+// segment of one column with a halo of H = (W-1)*tau + W + 1 sites on each side (SEGMENT,
+// temporal blocking: windows of W sites shrink the valid region by at most W-1 sites per side
+// per sub-step; the extra sites keep the one after the core valid for pair records).  Epoch e
+// covers sub-steps [n_begin + e*tau, ... + tau).  W = 3 for the PCPD, n+1 for the n-tuple
+// processes (TCPD, QCPD).
 // Items are popped in list order from a device counter by persistent CTAs; an item of epoch
 // e > 0 first waits (bounded, acquire) until the tiles it reads -- itself and, for segments,
 // its two neighbours -- have completed epoch e-1.  Epoch e reads lattice buffer e&1 and

@@ -8,7 +8,9 @@
 // draw u with integer thresholds floor(rate*2^32), bit-sliced over 32 random "planes" and
 // evaluated most-significant plane first with an early exit -- the exact generalisation of
 // the dyadic AND/OR masks of Sec. 4.2-4.3.  Random words come from Philox4x32-10 (Salmon et
-// al., SC'11) keyed by the seed and counted by (window, sub-step, group, tag|block).
+// al., SC'11) keyed by the seed and counted by (window, sub-step, group, tag|block).  The
+// triplet and quadruplet processes (TCPD, QCPD) use the same draws on windows of 4 and 5
+// sites (window_update_n).
 #pragma once
 #ifndef __CUDACC_RTC__
 #include <cstdint>
