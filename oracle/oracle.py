@@ -178,7 +178,9 @@ def rs_run(state: np.ndarray, p: float, d: float, seed: int, a_begin: int, a_end
 
 def paper_thresholds(p: float, d: float, m: int, n_dec: int):
     """(T_d, T_c) of the paper's scheme: d must be a multiple of 2^-m (T_d = d*2^m), and
-    p*2^n_dec <= 1 (T_c = floor(p*2^n_dec*2^32), 2^32 meaning always)."""
+    p*2^n_dec <= 1 (T_c = floor(p*2^n_dec*2^32), 2^32 meaning always); m, n_dec <= 16."""
+    if not (0 <= m <= 16 and 0 <= n_dec <= 16):
+        raise ValueError("m and n_dec must lie in [0, 16]")
     td = d * (1 << m)
     if td != int(td) or not (0 <= td <= (1 << m)):
         raise ValueError("d must be a multiple of 2^-m in [0, 1]")

@@ -59,6 +59,45 @@ def test_substep_of_time_matches_oracle(lib, oracle_mod):
             assert pcpd.substep_of_time(L, t) == oracle_mod.substep_of_time(L, t)
 
 
+def test_tuple_substep_of_time_matches_oracle(lib, oracle_mod):
+    from paper_1301_6082_gb300 import pcpd
+    for n in (3, 4):
+        for L in (n + 1, 10, 1024, 65536, 999999):
+            for t in (0, 1, 2, 1000, 10**6):
+                assert pcpd.substep_of_time(L, t, n) == oracle_mod.substep_of_time(L, t, n)
+    assert pcpd.substep_of_time(4, 10, 4) == 0          # shorter than one window
+    assert pcpd.substep_of_time(100, 10, 5) == 0        # no such tuple size
+
+
+def test_paper_thresholds_match_oracle(lib, oracle_mod):
+    from paper_1301_6082_gb300 import pcpd
+    rng = np.random.default_rng(11)
+    for _ in range(300):
+        m, n_dec = int(rng.integers(0, 17)), int(rng.integers(0, 17))
+        d = int(rng.integers(0, (1 << m) + 1)) / float(1 << m)
+        p = float(rng.random()) / float(1 << n_dec)
+        assert pcpd.paper_thresholds(p, d, m, n_dec) == oracle_mod.paper_thresholds(p, d, m, n_dec), (p, d, m, n_dec)
+    for bad in ((0.3, 0.5, 1, 2), (0.1, 0.3, 2, 0), (0.1, 0.5, 17, 0), (-0.1, 0.5, 1, 0)):
+        with pytest.raises(pcpd.PcpdError):
+            pcpd.paper_thresholds(*bad)
+        with pytest.raises(ValueError):
+            oracle_mod.paper_thresholds(*bad)
+
+
+def test_thresholds_property_random_doubles(lib, oracle_mod):
+    """Library and oracle agree on the thresholds for arbitrary doubles in [0, 1] (including
+    the edges and values one ulp from them)."""
+    hyp = pytest.importorskip("hypothesis")
+    st = pytest.importorskip("hypothesis.strategies")
+    from paper_1301_6082_gb300 import pcpd
+
+    @hyp.settings(max_examples=400, deadline=None)
+    @hyp.given(st.floats(0.0, 1.0), st.floats(0.0, 1.0))
+    def check(p, d):
+        assert pcpd.thresholds(p, d) == oracle_mod.thresholds(p, d)[:2]
+    check()
+
+
 def test_no_cuda_device_fails_loudly(lib):
     import torch
     if torch.cuda.is_available():
