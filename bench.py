@@ -552,6 +552,8 @@ def main():
                 "kernel": f"{kname}; tiles {plan0['core']}+2x{plan0['halo']} sites, tau={plan0['tau']}",
                 "peak_note": f"{sm_count} SMs x {WIDE_MUL_LANES} wide-multiply / {LOGIC_LANES} logic lanes x "
                              f"{sm_max_mhz:.0f} MHz (derived; lane rates measured, see DESIGN.md)",
+                "achieved_note": "algorithmic wide multiplies of all sweep launches in the timed region "
+                                 "(the three runs on their own streams) / the region's CUDA-event duration",
                 "wide_multiplies_per_item": round(mul_item, 2), "logic_ops_per_item": round(logic_item, 2),
                 "expected_philox_blocks_per_item": [round(o[1], 3) for o in ops_item],
                 "frac_of_issue_slots": (alg_ops / (ms / 1e3)) / 1e12 / issue_peak}
