@@ -150,7 +150,7 @@ int device_check() {
   int dev = 0, major = 0;
   CU(cudaGetDevice(&dev));
   CU(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev));
-  if (major != 10) return fail(PCPD_ENODEV, "device %d has compute capability %d.x; this build targets sm_103a", dev, major);
+  if (major != 10) return fail(PCPD_ENODEV, "device %d has compute capability %d.x; the library is compiled for sm_103a", dev, major);
   return PCPD_OK;
 }
 
