@@ -1,7 +1,7 @@
 """The index-checked debug build (libpcpd_debug.so, -DPCPD_DEBUG): on a spread of plans -- whole
 rings, segmented tiles, multi-column tiles, the n-tuple windows, batches, the paper's scheme --
 no kernel forms an out-of-range shared- or global-memory index, and the results equal the
-release build's bit for bit.  (compute-sanitizer is not available here; this stands in.)"""
+release build's bit for bit (a stand-in for a memory sanitizer)."""
 import json
 import os
 import subprocess
