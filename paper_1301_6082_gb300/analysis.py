@@ -17,3 +17,26 @@ def effective_exponent(times, rho):
     lt, lr = np.log(t), np.log(r)
     delta = -(lr[1:] - lr[:-1]) / (lt[1:] - lt[:-1])
     return np.exp(0.5 * (lt[1:] + lt[:-1])), np.exp(0.5 * (lr[1:] + lr[:-1])), delta
+
+
+def jackknife_effective_exponent(times, rho_replicas):
+    """Mean density over independent replicas (seeds, or 128-sample phase groups) with
+    jackknife standard errors, and delta_eff of the mean with jackknife errors.
+
+    rho_replicas: [R][T] densities of R >= 2 independent replicas at the record times.
+    Returns (rho_mean, rho_err, t_mid, delta, delta_err); delta is effective_exponent of the
+    mean.  The jackknife recomputes delta_eff with each replica left out in turn:
+    err^2 = (R-1)/R * sum_j (delta_(j) - mean_j delta_(j))^2."""
+    x = np.asarray(rho_replicas, dtype=np.float64)
+    if x.ndim != 2 or x.shape[0] < 2:
+        raise ValueError("need at least two replicas")
+    R = x.shape[0]
+    mean = x.mean(0)
+    loo = (x.sum(0)[None, :] - x) / (R - 1)          # leave-one-out means
+    rho_err = np.sqrt((R - 1) / R * ((loo - loo.mean(0)) ** 2).sum(0))
+    tm, _, delta = effective_exponent(times, mean)
+    deltas = np.array([effective_exponent(times, row)[2] for row in loo])
+    if deltas.shape[1] != delta.shape[0]:
+        raise ValueError("a leave-one-out mean has non-positive entries where the mean has none")
+    delta_err = np.sqrt((R - 1) / R * ((deltas - deltas.mean(0)) ** 2).sum(0))
+    return mean, rho_err, tm, delta, delta_err

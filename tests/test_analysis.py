@@ -29,3 +29,27 @@ def test_correction_to_scaling_converges():
 def test_skips_non_positive_entries():
     tm, rm, de = effective_exponent([0, 1, 2, 4], [1.0, 0.5, 0.0, 0.25])
     assert len(de) == 1 and np.isclose(de[0], -np.log(0.25 / 0.5) / np.log(4 / 1))
+
+
+def test_jackknife_error_of_the_mean_is_the_standard_error():
+    from paper_1301_6082_gb300.analysis import jackknife_effective_exponent
+    rng = np.random.default_rng(4)
+    t = np.array(log_times(10**4, 30), dtype=float)
+    R = 16
+    reps = (t ** -0.3)[None, :] * (1 + 0.05 * rng.standard_normal((R, t.size)))
+    mean, err, tm, de, de_err = jackknife_effective_exponent(t, reps)
+    np.testing.assert_allclose(mean, reps.mean(0), rtol=1e-14)
+    # for a linear statistic the jackknife error equals the usual standard error of the mean
+    np.testing.assert_allclose(err, reps.std(0, ddof=1) / np.sqrt(R), rtol=1e-10)
+    assert de.shape == de_err.shape == tm.shape and np.all(de_err > 0)
+    # the exponent is recovered within a few of its own error bars on the later intervals
+    assert np.all(np.abs(de[-10:] - 0.3) < 5 * de_err[-10:] + 1e-3)
+
+
+def test_jackknife_identical_replicas_have_zero_error():
+    from paper_1301_6082_gb300.analysis import jackknife_effective_exponent
+    t = np.array(log_times(1000, 12), dtype=float)
+    reps = np.tile(2.0 * t ** -0.5, (5, 1))
+    mean, err, _, de, de_err = jackknife_effective_exponent(t, reps)
+    assert np.all(err < 1e-15) and np.all(de_err < 1e-12)
+    np.testing.assert_allclose(de, 0.5, rtol=1e-12)

@@ -37,6 +37,10 @@ def test_p_sweep_matches_lone_runs(P):
         assert np.all(out[p]["rho_pair"] <= out[p]["rho"])
     # more annihilation, faster decay
     assert out[0.2]["rho"][-1] < out[0.12]["rho"][-1]
+    # two seeds: jackknife errors come with the means
+    for p in ps:
+        assert out[p]["rho_err"].shape == out[p]["rho"].shape and np.all(out[p]["rho_err"] >= 0)
+        assert out[p]["delta_eff_err"].shape == out[p]["delta_eff"][1].shape
 
 
 def test_p_sweep_tcpd_matches_lone_runs(P):
