@@ -147,10 +147,14 @@ int device_check() {
   cudaError_t e = cudaGetDeviceCount(&n);
   if (e != cudaSuccess || n == 0)
     return fail(PCPD_ENODEV, "no CUDA device (%s)", e == cudaSuccess ? "count 0" : cudaGetErrorString(e));
-  int dev = 0, major = 0;
+  int dev = 0, major = 0, minor = 0;
   CU(cudaGetDevice(&dev));
   CU(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev));
-  if (major != 10) return fail(PCPD_ENODEV, "device %d has compute capability %d.x; the library is compiled for sm_103a", dev, major);
+  CU(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev));
+  // sm_103a code runs on compute capability 10.3 only (the "a" features do not carry over)
+  if (major != 10 || minor != 3)
+    return fail(PCPD_ENODEV, "device %d has compute capability %d.%d; the library is compiled for sm_103a (10.3)",
+                dev, major, minor);
   return PCPD_OK;
 }
 
@@ -444,20 +448,32 @@ int make_plan(pcpd_t *h, const pcpd_params *prm) {
   return PCPD_OK;
 }
 
+// Device buffers allocated for a handle but not yet handed to it: freed on an early return
+// (an error), so that the handle keeps its old buffers and nothing leaks.
+struct FreeUnlessKept {
+  void **p[3];
+  bool keep = false;
+  ~FreeUnlessKept() {
+    if (keep) return;
+    for (void **q : p)
+      if (q && *q) cudaFree(*q);
+  }
+};
+
 int ensure_records(pcpd_t *h, size_t need) {
   if (need <= h->rec_cap) return PCPD_OK;
   size_t cap = h->rec_cap ? h->rec_cap : 64;
   while (cap < need) cap *= 2;
   unsigned long long *nt = nullptr, *np = nullptr;
   uint32_t *ns = nullptr;
-  CU(cudaMalloc(&nt, cap * sizeof(unsigned long long)));
-  CU(cudaMalloc(&np, cap * sizeof(unsigned long long)));
+  FreeUnlessKept pending{{(void **)&nt, (void **)&np, (void **)&ns}};
+  int rc = dev_alloc((void **)&nt, cap * sizeof(unsigned long long), "record totals");
+  if (!rc) rc = dev_alloc((void **)&np, cap * sizeof(unsigned long long), "record pair counts");
+  if (!rc && h->per_sample) rc = dev_alloc((void **)&ns, cap * (size_t)h->S * sizeof(uint32_t), "per-sample records");
+  if (rc) return rc;
   CU(cudaMemsetAsync(nt, 0, cap * sizeof(unsigned long long), h->stream));
   CU(cudaMemsetAsync(np, 0, cap * sizeof(unsigned long long), h->stream));
-  if (h->per_sample) {
-    CU(cudaMalloc(&ns, cap * (size_t)h->S * sizeof(uint32_t)));
-    CU(cudaMemsetAsync(ns, 0, cap * (size_t)h->S * sizeof(uint32_t), h->stream));
-  }
+  if (h->per_sample) CU(cudaMemsetAsync(ns, 0, cap * (size_t)h->S * sizeof(uint32_t), h->stream));
   const size_t have = h->rec_times.size();
   if (have) {
     CU(cudaMemcpyAsync(nt, h->d_rec_total, have * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, h->stream));
@@ -466,6 +482,7 @@ int ensure_records(pcpd_t *h, size_t need) {
       CU(cudaMemcpyAsync(ns, h->d_rec_sample, have * (size_t)h->S * sizeof(uint32_t), cudaMemcpyDeviceToDevice, h->stream));
   }
   CU(cudaStreamSynchronize(h->stream));
+  pending.keep = true;
   cudaFree(h->d_rec_total);
   cudaFree(h->d_rec_pairs);
   cudaFree(h->d_rec_sample);
@@ -483,7 +500,9 @@ int ensure_rec_sub(pcpd_t *h, size_t need) {
   CU(cudaStreamSynchronize(h->stream));
   cudaFree(h->d_rec_sub);
   h->d_rec_sub = nullptr;
-  CU(cudaMalloc(&h->d_rec_sub, cap * sizeof(uint32_t)));
+  h->rec_sub_cap = 0;   // no buffer until the new one exists
+  const int rc = dev_alloc((void **)&h->d_rec_sub, cap * sizeof(uint32_t), "record sub-steps");
+  if (rc) return rc;
   h->rec_sub_cap = cap;
   return PCPD_OK;
 }
@@ -1223,13 +1242,16 @@ int run_multi(cudaStream_t stream, uint32_t *d_ctl, unsigned long long **d_items
       CU(cudaStreamSynchronize(stream));
       cudaFree(*d_items);
       *d_items = nullptr;
-      CU(cudaMalloc(d_items, items.size() * sizeof(unsigned long long)));
+      *items_cap = 0;
+      const int rc = dev_alloc((void **)d_items, items.size() * sizeof(unsigned long long), "batch work items");
+      if (rc) return rc;
       *items_cap = items.size();
     }
     if (items.size() > gc.h_items_cap) {
       CU(cudaStreamSynchronize(stream));
       if (gc.h_items) cudaFreeHost(gc.h_items);
       gc.h_items = nullptr;
+      gc.h_items_cap = 0;
       CU(cudaMallocHost(&gc.h_items, items.size() * sizeof(unsigned long long)));
       gc.h_items_cap = items.size();
     }
@@ -2092,9 +2114,11 @@ int paper_ensure_records(pcpd_paper_t *h, size_t need) {
   while (cap < need) cap *= 2;
   unsigned long long *nt = nullptr, *ns = nullptr;
   uint32_t *nsys = nullptr;
-  CU(cudaMalloc(&nt, cap * sizeof(unsigned long long)));
-  CU(cudaMalloc(&ns, cap * sizeof(unsigned long long)));
-  CU(cudaMalloc(&nsys, cap * (size_t)h->systems * sizeof(uint32_t)));
+  FreeUnlessKept pending{{(void **)&nt, (void **)&ns, (void **)&nsys}};
+  int rc = dev_alloc((void **)&nt, cap * sizeof(unsigned long long), "record totals");
+  if (!rc) rc = dev_alloc((void **)&ns, cap * sizeof(unsigned long long), "record steps");
+  if (!rc) rc = dev_alloc((void **)&nsys, cap * (size_t)h->systems * sizeof(uint32_t), "per-system records");
+  if (rc) return rc;
   CU(cudaMemsetAsync(nt, 0, cap * sizeof(unsigned long long), h->stream));
   CU(cudaMemsetAsync(nsys, 0, cap * (size_t)h->systems * sizeof(uint32_t), h->stream));
   const size_t have = h->rec_steps.size();
@@ -2104,6 +2128,7 @@ int paper_ensure_records(pcpd_paper_t *h, size_t need) {
                        cudaMemcpyDeviceToDevice, h->stream));
   }
   CU(cudaStreamSynchronize(h->stream));
+  pending.keep = true;
   cudaFree(h->d_rec_total);
   cudaFree(h->d_rec_step);
   cudaFree(h->d_rec_sys);
