@@ -167,12 +167,29 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 6 : 1) k_paper_sweep(const
   uint32_t s0 = 0u, s1 = 0u, s2 = 0u, s3 = 0u;  // local-site words of this lane's group
   uint32_t q0 = begin >> 2;
 
+  // The thread's stream blocks differ only in B: x0 = w, x2 = sys are fixed, and x3 = tag|B>>32
+  // changes once per 2^32 blocks.  What depends on (w, sys, B>>32) alone is computed once:
+  // then a block needs 16 of its 20 multiplies (rounds 1-3 share most of their products).
+  const uint32_t A0 = __umulhi(sys, kPhiloxM1) ^ P.rk.k0[0];   // round-1 x0 = A0 ^ (uint32_t)B
+  const uint32_t E = (w * kPhiloxM0) ^ P.rk.k1[1];             // round-2 x2 = hi(M0 x0) ^ E
+  uint32_t C2 = 0u, C3h = 0u, C3l = 0u, hb_cached = 0u;
+  auto prefix = [&](uint32_t hb) {
+    const uint32_t x2p = __umulhi(w, kPhiloxM0) ^ P.rk.k1[0] ^ ((kTagPaper << 28) | hb);
+    const uint32_t C1 = __umulhi(x2p, kPhiloxM1) ^ (sys * kPhiloxM1) ^ P.rk.k0[1];   // round-2 x0
+    C2 = x2p * kPhiloxM1;                                                           // round-2 x1
+    C3h = __umulhi(C1, kPhiloxM0) ^ P.rk.k1[2];
+    C3l = C1 * kPhiloxM0;                                                           // round-3 x3
+    hb_cached = hb;
+  };
+  prefix(0u);
+
   // one group of 4 steps (4q .. 4q+3); EDGE: the group may extend past [begin, end);
   // HASREC: a record step may fall inside (else the group has no branch and the compiler can
   // interleave its four steps)
   auto group = [&](uint32_t q, auto edge, auto hasrec) {
     constexpr bool EDGE = decltype(edge)::value;
     constexpr bool HASREC = decltype(hasrec)::value;
+    constexpr bool FAST = !EDGE;   // blocks from the shared prefix (one value of B>>32)
     const uint32_t qi = (q - q0) & 31u;
     if (qi == 0u) {
       // lane i draws the local sites of the 4 steps of group q + i
@@ -191,9 +208,29 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 6 : 1) k_paper_sweep(const
         const uint32_t k = j * nw + i;
         if ((k & 3u) == 0u) {
           const unsigned long long B = B0 + (k >> 2);
-          uint32_t x0 = w, x1 = (uint32_t)B, x2 = sys, x3 = (kTagPaper << 28) | (uint32_t)(B >> 32);
-          philox4x32_10_rk(x0, x1, x2, x3, P.rk);
-          c0 = x0, c1 = x1, c2 = x2, c3 = x3;
+          if (FAST) {
+            const uint32_t x0p = A0 ^ (uint32_t)B;
+            const uint32_t x2pp = __umulhi(x0p, kPhiloxM0) ^ E;
+            const uint32_t x3pp = x0p * kPhiloxM0;
+            uint32_t x0 = __umulhi(x2pp, kPhiloxM1) ^ C2 ^ P.rk.k0[2];
+            uint32_t x1 = x2pp * kPhiloxM1;
+            uint32_t x2 = C3h ^ x3pp;
+            uint32_t x3 = C3l;
+#pragma unroll
+            for (int rr = 3; rr < 10; ++rr) {
+              const uint32_t h0 = __umulhi(x0, kPhiloxM0), l0 = x0 * kPhiloxM0;
+              const uint32_t h1 = __umulhi(x2, kPhiloxM1), l1 = x2 * kPhiloxM1;
+              x0 = h1 ^ x1 ^ P.rk.k0[rr];
+              x1 = l1;
+              x2 = h0 ^ x3 ^ P.rk.k1[rr];
+              x3 = l0;
+            }
+            c0 = x0, c1 = x1, c2 = x2, c3 = x3;
+          } else {
+            uint32_t x0 = w, x1 = (uint32_t)B, x2 = sys, x3 = (kTagPaper << 28) | (uint32_t)(B >> 32);
+            philox4x32_10_rk(x0, x1, x2, x3, P.rk);
+            c0 = x0, c1 = x1, c2 = x2, c3 = x3;
+          }
         }
         const uint32_t u = pick4(c0, c1, c2, c3, k & 3u);
         if ((int)i < (int)m) {
@@ -243,6 +280,13 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 6 : 1) k_paper_sweep(const
     if (head) group(q++, PaperEdge<true>{}, PaperEdge<true>{});
     const uint32_t q_full_end = ((end & 3u) == 0u) ? q1 + 1u : q1;  // groups entirely inside
     for (; q < q_full_end; ++q) {
+      const unsigned long long B0 = (unsigned long long)q * nw;
+      const uint32_t hb = (uint32_t)(B0 >> 32);
+      if (hb != (uint32_t)((B0 + nw - 1u) >> 32)) {   // B>>32 changes inside the group
+        group(q, PaperEdge<true>{}, PaperEdge<true>{});
+        continue;
+      }
+      if (hb != hb_cached) prefix(hb);
       if ((next_rec >> 2) == q) group(q, PaperEdge<false>{}, PaperEdge<true>{});
       else group(q, PaperEdge<false>{}, PaperEdge<false>{});
     }

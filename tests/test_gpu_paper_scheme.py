@@ -188,6 +188,32 @@ def test_paper_scheme_near_the_step_counter_limit(P, oracle_mod):
     np.testing.assert_array_equal(lat, ref)
 
 
+@pytest.mark.parametrize("m,n_dec,p,S_w", [(1, 2, 0.15, 64), (2, 2, 0.2, 32), (3, 3, 0.1, 64), (5, 1, 0.3, 32)])
+def test_paper_scheme_across_block_index_2_32(P, oracle_mod, m, n_dec, p, S_w):
+    """A run across the step where the stream's block index B = n_w*t/4 reaches 2^32: the
+    kernel forms most of a block's first three rounds once per thread for each value of
+    B >> 32, and a group of four steps whose blocks straddle 2^32 takes the full counter.
+    n_w = 5 and 6 straddle inside a group, n_w = 8 reaches 2^32 at a group start; m = 5 runs
+    the kernel with (m, n_dec) read at run time."""
+    n_loc, systems = 4, 3
+    n_w = m + n_dec + 2
+    t_cross = ((1 << 32) * 4 + n_w - 1) // n_w          # first step whose blocks have B >= 2^32
+    step0 = t_cross - 37
+    rng = np.random.default_rng(31 + m)
+    st = (rng.random((systems, 32 * n_loc * S_w)) < 0.7).astype(np.uint8)
+    d = 0.5
+    recs = [step0 + 10, t_cross, step0 + 90]
+    with P.PaperScheme(n_loc, S_w, systems, p, d, m, n_dec, seed=2024) as h:
+        h.set_lattice(sites_to_words(st, n_loc, S_w), step0)
+        h.run(90, recs)
+        got = h.counts()
+        lat = words_to_sites(h.lattice(), n_loc, S_w)
+    ref = st.copy()
+    want = oracle_mod.paper_run(ref, n_loc, S_w, p, d, m, n_dec, 2024, step0, step0 + 90, recs)
+    np.testing.assert_array_equal(got, want)
+    np.testing.assert_array_equal(lat, ref)
+
+
 def test_paper_scheme_largest_system_that_fits_shared_memory(P, oracle_mod):
     """The longest ring one CTA can hold (n_loc*S_w words up to the shared-memory limit), one
     sampled system against the oracle; one more local word per thread is refused."""
