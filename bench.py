@@ -450,6 +450,9 @@ def main():
     ap.add_argument("--paper-only", action="store_true",
                     help="run only the paper-scheme leg (for profiling) and print its JSON")
     ap.add_argument("--paper-mcs", type=int, default=1000)
+    ap.add_argument("--stream-only", action="store_true",
+                    help="run only the HBM-streamed leg (for profiling) and print its JSON")
+    ap.add_argument("--stream-substeps", type=int, default=2048)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -466,6 +469,9 @@ def main():
     torch.cuda.set_device(local)
     if args.paper_only:
         print(json.dumps({"paper_scheme": paper_leg(pcpd, mcs=args.paper_mcs)}), flush=True)
+        return 0
+    if args.stream_only:
+        print(json.dumps({"streamed": stream_leg(pcpd, substeps=args.stream_substeps)}), flush=True)
         return 0
     dist = None
     if world > 1:
@@ -607,7 +613,7 @@ def main():
     sims = []
     batch = batch_leg(pcpd) if not args.no_batch else None
     serving = serving_leg(pcpd) if not args.no_serve else None
-    streamed = stream_leg(pcpd) if not args.no_stream else None
+    streamed = stream_leg(pcpd, substeps=args.stream_substeps) if not args.no_stream else None
     paper = paper_leg(pcpd, mcs=args.paper_mcs) if not args.no_paper else None
     tuples = tuple_leg(pcpd) if not args.no_tuples else None
 
