@@ -33,8 +33,9 @@ from paper_1301_6082_gb300.workloads import SMEM_L65536, batch_instances, log_ti
 
 METRIC = "attempted site updates/s"
 # dram__bytes_read.sum + dram__bytes_write.sum of one bench-size launch of the specialised
-# sweep (one run advanced 2000 MCS), 1-pass ncu capture (profiles/pcpd_jit_sweep_L65536_S4096.md)
-TRAFFIC_PER_LAUNCH = 36.61e6 + 748.18e6
+# sweep (one run advanced 2000 MCS; two 256-thread CTAs per SM, tiles 21848 + 2 x 132 sites,
+# tau = 64), 1-pass ncu capture (profiles/pcpd_jit_sweep_L65536_S4096.md)
+TRAFFIC_PER_LAUNCH = 38.21e6 + 1767.53e6
 UNIT = "attempts/s"
 
 

@@ -369,8 +369,12 @@ int jit_function(uint32_t td, uint32_t tda, uint32_t W, CUfunction *out) {
 
 // Tile plan.  Columns that fit in shared memory run as RING tiles (whole columns, gpi of them
 // per CTA when they are short, so that a CTA has enough windows per sub-step); longer columns
-// are cut into equal SEGMENT tiles with a halo of 2*tau sites.  No plan changes a result bit.
-int make_plan(pcpd_t *h, const pcpd_params *prm) {
+// are cut into equal SEGMENT tiles with a halo of (W-1)*tau + W + 1 sites.  PAIRED: SEGMENT
+// tiles are sized so that two CTAs of 256 threads share an SM (one CTA's barriers and
+// deferred-window tail overlap the other's first pass), with tau = 64; otherwise one CTA of
+// kSweepThreads per SM holds the largest tile, tau = 128 (batched launches, which run every
+// instance with one CTA shape, and the allocation-free sweep).  No plan changes a result bit.
+int make_plan(pcpd_t *h, const pcpd_params *prm, bool paired = false) {
   int optin = 0, dev = 0, sms = 0;
   int rc = smem_optin(&optin);
   if (rc) return rc;
@@ -378,6 +382,15 @@ int make_plan(pcpd_t *h, const pcpd_params *prm) {
   CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const size_t list_words = pcpdk::sweep_queue_words(32);
   const size_t avail_words = ((size_t)optin - kStaticSmem) / 4 - list_words;
+  // shared memory each of two CTAs on one SM may hold
+  size_t pair_words = 0;
+  if (paired) {
+    int per_sm = 0, reserved = 0;
+    CU(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    CU(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev));
+    const size_t each = (size_t)per_sm / 2u > (size_t)reserved ? (size_t)per_sm / 2u - (size_t)reserved : 0u;
+    pair_words = each > kStaticSmem + 4u * list_words ? (each - kStaticSmem) / 4u - list_words : 0u;
+  }
   const uint32_t L = h->L;
   const uint32_t seg_override = prm ? prm->plan_seg_sites : 0;
   h->tau = (prm && prm->plan_tau) ? prm->plan_tau : 128u;
@@ -404,14 +417,19 @@ int make_plan(pcpd_t *h, const pcpd_params *prm) {
   } else {
     h->ring = false;
     h->gpi = 1;
+    if (paired && !(prm && prm->plan_tau)) h->tau = 64u;
     // W-1 sites per sub-step, + one valid site past the core (pair records), + margin
     h->halo = (h->W - 1u) * h->tau + h->W + 1u;
     uint32_t core;
     if (seg_override) {
       core = seg_override;
     } else {
-      const size_t max_core = avail_words > 2u * h->halo ? avail_words - 2u * h->halo : 0;
-      if (max_core < 1024) return fail(PCPD_EINVAL, "temporal block tau=%u too large for shared memory", h->tau);
+      const size_t budget = paired ? pair_words : avail_words;
+      const size_t max_core = budget > 2u * h->halo ? budget - 2u * h->halo : 0;
+      if (max_core < 1024) {
+        if (paired) return make_plan(h, prm, false);
+        return fail(PCPD_EINVAL, "temporal block tau=%u too large for shared memory", h->tau);
+      }
       uint32_t nseg = (uint32_t)((L + max_core - 1) / max_core);
       for (;; ++nseg) {
         core = (L + nseg - 1) / nseg;
@@ -426,7 +444,7 @@ int make_plan(pcpd_t *h, const pcpd_params *prm) {
     // a tile shorter than L - 4W sees fewer candidate windows than the ring has
     if (h->n_seg < 2 || h->tile_words + 4u * h->W > L)
       return fail(PCPD_EINVAL, "segmented plan needs >= 2 tiles each shorter than L-4W (L=%u, core=%u, halo=%u)", L, core, h->halo);
-    h->threads = pcpdk::kSweepThreads;
+    h->threads = paired ? 256u : pcpdk::kSweepThreads;
   }
   if (prm && prm->plan_threads) {
     if (prm->plan_threads % 32 || prm->plan_threads > pcpdk::kSweepThreads || prm->plan_threads < 64)
@@ -438,6 +456,7 @@ int make_plan(pcpd_t *h, const pcpd_params *prm) {
   if (rc) return rc;
   int per_sm = 0;
   CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel(false, h->W), (int)h->threads, h->dyn_smem));
+  if (paired && !h->ring && per_sm < 2) return make_plan(h, prm, false);   // the pair does not fit
   if (per_sm < 1) return fail(PCPD_EINVAL, "tile plan does not fit one CTA per SM");
   h->grid = per_sm * sms;
   const uint64_t tiles = (uint64_t)(h->G / h->gpi) * h->n_seg;
@@ -662,7 +681,13 @@ uint64_t pcpd_substep_of_time_n(uint32_t L, uint32_t tuple, uint64_t t) {
   return (tuple == 1u || tuple > 4u || L < W) ? 0 : substep_of_time(L, t, W);
 }
 
-int pcpd_create_ex(const pcpd_params *prm, pcpd_t **out) {
+}  // extern "C"
+
+namespace {
+
+// A handle; BATCH_MEMBER: it runs in batched launches (one CTA shape for every instance of a
+// launch), so its SEGMENT tiles take the one-CTA-per-SM plan.
+int create_handle(const pcpd_params *prm, pcpd_t **out, bool batch_member) {
   if (!prm || !out) return fail(PCPD_EINVAL, "NULL argument");
   *out = nullptr;
   if (prm->L < 3 || prm->L >= (1u << 30)) return fail(PCPD_EINVAL, "L must satisfy 3 <= L < 2^30 (L=%u)", prm->L);
@@ -703,7 +728,7 @@ int pcpd_create_ex(const pcpd_params *prm, pcpd_t **out) {
     pcpd_destroy(h);
     return code;
   };
-  rc = make_plan(h, prm);
+  rc = make_plan(h, prm, !batch_member);
   if (rc) return bail(rc);
   if (prm->stream) {
     h->stream = (cudaStream_t)prm->stream;
@@ -757,6 +782,12 @@ int pcpd_create_ex(const pcpd_params *prm, pcpd_t **out) {
   *out = h;
   return PCPD_OK;
 }
+
+}  // namespace
+
+extern "C" {
+
+int pcpd_create_ex(const pcpd_params *prm, pcpd_t **out) { return create_handle(prm, out, false); }
 
 pcpd_t *pcpd_create(uint32_t L, uint32_t samples, double p, double d, uint64_t seed) {
   pcpd_params prm;
@@ -1385,7 +1416,7 @@ int pcpd_batch_add(pcpd_batch_t *b, const pcpd_params *prm, uint64_t steps_mcs,
   p2.dev_bytes = 0;
   p2.jit = -1;   // batched launches run the generic engine (one kernel for many thresholds)
   pcpd_t *h = nullptr;
-  int rc = pcpd_create_ex(&p2, &h);
+  int rc = create_handle(&p2, &h, true);
   if (rc) return rc;
   const uint64_t n_end = steps_mcs ? substep_of_time(h->L, steps_mcs, h->W) : 0;
   if (n_end > 0xFFFFFFFFull) {
@@ -1566,7 +1597,7 @@ void server_loop(pcpd_server_t *sv) {
       p2.stream = sv->stream;
       p2.dev_lattice = nullptr;
       p2.jit = -1;   // serving rounds run the generic engine
-      int rc = pcpd_create_ex(&p2, &r->h);
+      int rc = create_handle(&p2, &r->h, true);
       if (rc == PCPD_OK) rc = ensure_records(r->h, r->rec_times.size());
       if (rc == PCPD_OK && !r->rec_times.empty()) {
         rc = ensure_rec_sub(r->h, r->rec_times.size());
@@ -1992,6 +2023,9 @@ extern "C" int pcpd_autotune(const pcpd_params *prm, uint32_t trial_substeps, pc
   if (prm->samples == 0 || prm->samples % 32 || prm->L < 3) return fail(PCPD_EINVAL, "bad L or samples");
   rc = make_plan(&base, nullptr);
   if (rc) return rc;
+  pcpd paired = base;   // the tile two CTAs per SM can hold
+  rc = make_plan(&paired, nullptr, true);
+  if (rc) return rc;
   struct Cand {
     uint32_t threads, seg, tau;
   };
@@ -2001,9 +2035,11 @@ extern "C" int pcpd_autotune(const pcpd_params *prm, uint32_t trial_substeps, pc
       if (th <= pcpdk::kSweepThreads && (th <= base.threads * 2u || th == 128u)) cands.push_back({th, 0u, 0u});
   } else {
     const uint32_t half = ((base.core / 2u) + 3u) & ~3u;
+    std::vector<uint32_t> segs = {base.core, half};
+    if (paired.core != base.core && paired.core != half) segs.push_back(paired.core);
     for (uint32_t th : {256u, 512u})
       for (uint32_t tau : {64u, 128u, 256u})
-        for (uint32_t seg : {base.core, half}) {
+        for (uint32_t seg : segs) {
           if (seg + 2u * ((base.W - 1u) * tau + base.W + 1u) + 4u * base.W > prm->L || (prm->L + seg - 1) / seg < 2)
             continue;
           cands.push_back({th, seg, tau});
