@@ -144,6 +144,36 @@ def test_segmented_plan_bit_exact_and_plan_invariant(P, oracle_mod, L, seg, tau,
     np.testing.assert_array_equal(a.lattice(), oracle_mod.pack(st))
 
 
+def test_default_plans_two_ctas_per_sm_alone_one_in_batches(P, oracle_mod):
+    """A lone instance whose columns exceed one CTA's shared memory runs two 256-thread CTAs
+    per SM (tau = 64); the same instance in a batch runs one 512-thread CTA per SM with the
+    largest tile (tau = 128). Both give the oracle's bits, and so does the one-CTA plan forced
+    on a lone instance."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    L, S, p, d, seed, mcs = 65536, 64, 0.15, 0.5, 5, 3
+    times = [1, 2, 3]
+    a = P.Pcpd(L, S, p, d, seed=seed, init=INIT_HALF)
+    pa = a.plan()
+    assert pa["ring"] == 0 and pa["threads"] == 256 and pa["tau"] == 64 and pa["grid"] == 2 * sms, pa
+    a.run(mcs, times)
+    c = P.Pcpd(L, S, p, d, seed=seed, init=INIT_HALF, plan_threads=512, plan_seg_sites=32768, plan_tau=128)
+    pc = c.plan()
+    assert pc["threads"] == 512 and pc["grid"] == sms, pc
+    c.run(mcs, times)
+    b = P.Batch()
+    i = b.add(L, S, p, d, seed, mcs, times, init=INIT_HALF)
+    b.run()
+    subs = [oracle_mod.substep_of_time(L, t) for t in times]
+    st = oracle_mod.init_state(L, S, INIT_HALF, seed)
+    tot, _, _ = oracle_mod.run(st, p, d, seed, 0, subs[-1], subs)
+    for got in (a.counts(), c.counts(), b.counts(i)):
+        np.testing.assert_array_equal(got, tot)
+    np.testing.assert_array_equal(a.lattice(), oracle_mod.pack(st))
+    np.testing.assert_array_equal(c.lattice(), oracle_mod.pack(st))
+    a.close(), c.close(), b.close()
+
+
 def test_resume_from_saved_state_is_exact(P):
     L, S, p, d, seed = 777, 96, 0.2, 0.4, 3
     a = P.Pcpd(L, S, p, d, seed=seed, init=INIT_HALF)
