@@ -63,8 +63,11 @@ typedef struct pcpd_params {
                             handle allocates (and frees) its own */
     size_t dev_bytes;    /* size of dev_lattice in bytes (ignored when dev_lattice is NULL) */
     int per_sample;      /* non-zero: also keep per-sample counts at every record */
-    /* plan override, 0 = automatic.  No plan changes a result bit. */
-    uint32_t plan_threads;   /* threads per CTA (multiple of 32, <= 1024) */
+    /* plan override, 0 = automatic.  No plan changes a result bit.  Automatic: columns that
+       fit one CTA's shared memory are whole-column tiles; longer columns are cut into tiles
+       sized for two 256-thread CTAs per SM with tau = 64 (handles in batches and servers:
+       one 512-thread CTA per SM with the largest tile, tau = 128). */
+    uint32_t plan_threads;   /* threads per CTA (multiple of 32 in [64, 512]) */
     uint32_t plan_seg_sites; /* core sites per tile for lattices that do not fit one CTA */
     uint32_t plan_tau;       /* sub-steps per tile residency (temporal block) */
     int autotune;            /* non-zero and no plan_* override: use the plan pcpd_autotune
@@ -143,7 +146,7 @@ typedef struct pcpd_plan_info {
     uint32_t gpi;        /* columns per tile (RING) */
     uint32_t threads;    /* threads per CTA */
     uint32_t core;       /* core sites per tile */
-    uint32_t halo;       /* halo sites per side (SEGMENT; 2*tau) */
+    uint32_t halo;       /* halo sites per side (SEGMENT; (W-1)*tau + W + 1, W = tuple + 1) */
     uint32_t tau;        /* sub-steps per tile residency */
     uint32_t n_seg;      /* tiles per column */
     uint32_t tiles;      /* tiles per epoch */
