@@ -395,7 +395,17 @@ int make_plan(pcpd_t *h, const pcpd_params *prm, bool paired = false) {
   const uint32_t seg_override = prm ? prm->plan_seg_sites : 0;
   h->tau = (prm && prm->plan_tau) ? prm->plan_tau : 128u;
   if (h->tau == 0u) return fail(PCPD_EINVAL, "plan_tau must be positive");
-  if (seg_override == 0 && L <= avail_words) {
+  // Segment tiles below this many core sites cost more in halo windows than they give.
+  constexpr uint32_t kMinCore = 4096u;
+  bool ring = seg_override == 0 && L <= avail_words;
+  if (paired && ring && h->G < (uint32_t)sms) {
+    // fewer whole columns than SMs would leave SMs idle: cut the columns into segments
+    // instead, when two segments of a useful length fit
+    const uint32_t tau = (prm && prm->plan_tau) ? prm->plan_tau : 64u;
+    const uint64_t halo = (uint64_t)(h->W - 1u) * tau + h->W + 1u;
+    if ((uint64_t)L >= 2u * (kMinCore + 2u * halo)) ring = false;
+  }
+  if (ring) {
     h->ring = true;
     h->core = L;
     h->halo = 0;
@@ -430,7 +440,11 @@ int make_plan(pcpd_t *h, const pcpd_params *prm, bool paired = false) {
         if (paired) return make_plan(h, prm, false);
         return fail(PCPD_EINVAL, "temporal block tau=%u too large for shared memory", h->tau);
       }
-      uint32_t nseg = (uint32_t)((L + max_core - 1) / max_core);
+      uint32_t nseg = std::max<uint32_t>(2u, (uint32_t)((L + max_core - 1) / max_core));
+      if (paired) {
+        // enough tiles per epoch for the two CTAs of every SM, while tiles stay long
+        while ((uint64_t)h->G * nseg < 2ull * (uint64_t)sms && (L + nseg) / (nseg + 1u) >= kMinCore) ++nseg;
+      }
       for (;; ++nseg) {
         core = (L + nseg - 1) / nseg;
         core = (core + 3u) & ~3u;   // keep tile starts 16-byte aligned
@@ -2033,6 +2047,8 @@ extern "C" int pcpd_autotune(const pcpd_params *prm, uint32_t trial_substeps, pc
   if (base.ring) {
     for (uint32_t th : {128u, 256u, 512u})
       if (th <= pcpdk::kSweepThreads && (th <= base.threads * 2u || th == 128u)) cands.push_back({th, 0u, 0u});
+    if (!paired.ring)   // too few columns for the SMs: the segment plan of a lone instance
+      for (uint32_t tau : {64u, 128u}) cands.push_back({paired.threads, paired.core, tau});
   } else {
     const uint32_t half = ((base.core / 2u) + 3u) & ~3u;
     std::vector<uint32_t> segs = {base.core, half};
