@@ -451,6 +451,8 @@ def main():
     ap.add_argument("--paper-only", action="store_true",
                     help="run only the paper-scheme leg (for profiling) and print its JSON")
     ap.add_argument("--paper-mcs", type=int, default=1000)
+    ap.add_argument("--batch-only", action="store_true",
+                    help="run only the 512-instance batch leg (for profiling) and print its JSON")
     ap.add_argument("--stream-only", action="store_true",
                     help="run only the HBM-streamed leg (for profiling) and print its JSON")
     ap.add_argument("--stream-substeps", type=int, default=2048)
@@ -470,6 +472,9 @@ def main():
     torch.cuda.set_device(local)
     if args.paper_only:
         print(json.dumps({"paper_scheme": paper_leg(pcpd, mcs=args.paper_mcs)}), flush=True)
+        return 0
+    if args.batch_only:
+        print(json.dumps({"batch": batch_leg(pcpd)}), flush=True)
         return 0
     if args.stream_only:
         print(json.dumps({"streamed": stream_leg(pcpd, substeps=args.stream_substeps)}), flush=True)
