@@ -1,7 +1,7 @@
 """CPU-side checks of the boundary: the library builds for sm_103a, loads, exports every
 entry point include/pcpd.h declares, and its host-only helpers (thresholds, time) agree with
 the oracle's.  No kernel is launched here."""
-import ctypes
+import ctypes as C
 import os
 import re
 
@@ -128,3 +128,33 @@ def test_c_example_builds_and_fails_loudly_without_a_device():
         return   # the GPU test covers the run itself
     r = subprocess.run([exe, "64", "32", "0.15", "0.5"], capture_output=True, text=True)
     assert r.returncode == 6 and "pcpd error 6" in r.stderr
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every struct the binding passes across the ABI has the header's size and field offsets
+    (a C program compiled against include/pcpd.h prints them)."""
+    import subprocess
+    from paper_1301_6082_gb300 import pcpd
+    structs = {"pcpd_params": pcpd.Params, "pcpd_plan_info": pcpd.PlanInfo,
+               "pcpd_server_config": pcpd.ServerConfig, "pcpd_server_stats": pcpd.ServerStats,
+               "pcpd_paper_params": pcpd.PaperParams}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pcpd.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} sizeof %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            name, key, val = line.split()
+            got[(name, key)] = int(val)
+    for name, cls in structs.items():
+        assert got[(name, "sizeof")] == C.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)
