@@ -170,6 +170,7 @@ def run_cpu_sample(budget_groups: int = 16, substeps: int = 300):
     dt = time.perf_counter() - t0
     attempts = S * (L // 3) * substeps
     return {"value": attempts / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "value_per_core": attempts / dt / cores,
             "sample": f"{budget_groups} groups ({S} samples) of L={L}, d=0.5 p=0.15, {substeps} sub-steps "
                       f"from full ({attempts:.3e} attempts, {dt:.1f} s)"}
 
@@ -428,7 +429,7 @@ def reference_arm(args, world, rank):
             "config": {"workload": SMEM_L65536["name"], "L": SMEM_L65536["L"], "samples": SMEM_L65536["S"],
                        "note": "each step: the CPU oracle on a bounded sample of the workload"},
             "cpu_baseline": {"kind": "oracle", "cores": res["cores"], "sample": res["sample"], "value": value,
-                             "unit": UNIT},
+                             "unit": UNIT, "value_per_core": value / res["cores"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
