@@ -174,6 +174,28 @@ def test_default_plans_two_ctas_per_sm_alone_one_in_batches(P, oracle_mod):
     a.close(), c.close(), b.close()
 
 
+@pytest.mark.parametrize("L,S,tuple_n", [(20000, 64, 2), (12001, 96, 2), (30011, 32, 3)])
+def test_short_columns_cut_into_segments_when_sms_would_idle(P, oracle_mod, L, S, tuple_n):
+    """Columns that fit one CTA but are fewer than the SMs: a lone instance cuts them into
+    segments (ragged last one included) instead of whole-column tiles; same bits as the
+    oracle, with records inside and at the end of the run."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    p, d, seed = 0.2, 0.4, 21
+    a = P.Pcpd(L, S, p, d, seed=seed, init=INIT_HALF, tuple_n=tuple_n)
+    plan = a.plan()
+    assert S // 32 < sms and plan["ring"] == 0 and plan["n_seg"] >= 2 and plan["core"] >= 4096, plan
+    times = [2, 5, 9]
+    a.run(times[-1], times)
+    subs = [oracle_mod.substep_of_time(L, t, tuple_n) for t in times]
+    st = oracle_mod.init_state(L, S, INIT_HALF, seed)
+    tot, _, _, prs = oracle_mod.run(st, p, d, seed, 0, subs[-1], subs, pairs=True, tuple_n=tuple_n)
+    np.testing.assert_array_equal(a.counts(), tot)
+    np.testing.assert_array_equal(a.pair_counts(), prs)
+    np.testing.assert_array_equal(a.lattice(), oracle_mod.pack(st))
+    a.close()
+
+
 def test_resume_from_saved_state_is_exact(P):
     L, S, p, d, seed = 777, 96, 0.2, 0.4, 3
     a = P.Pcpd(L, S, p, d, seed=seed, init=INIT_HALF)
