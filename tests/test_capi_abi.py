@@ -158,3 +158,13 @@ def test_binding_structs_match_the_header_layout(tmp_path):
         assert got[(name, "sizeof")] == C.sizeof(cls), name
         for field, _ in cls._fields_:
             assert got[(name, field)] == getattr(cls, field).offset, (name, field)
+
+
+def test_oracle_does_not_use_the_product():
+    """The oracle shares no code with the CUDA path: it imports no package module and includes
+    none of the library's headers or sources."""
+    pat = re.compile(r"paper_1301_6082_gb300|pcpd\.h|pcpd_kernels|pcpd_engine|pcpd_capi|libpcpd")
+    odir = os.path.join(ROOT, "oracle")
+    for f in os.listdir(odir):
+        if f.endswith((".py", ".c", ".h")):
+            assert not pat.search(open(os.path.join(odir, f)).read()), f
