@@ -40,3 +40,21 @@ def jackknife_effective_exponent(times, rho_replicas):
         raise ValueError("a leave-one-out mean has non-positive entries where the mean has none")
     delta_err = np.sqrt((R - 1) / R * ((deltas - deltas.mean(0)) ** 2).sum(0))
     return mean, rho_err, tm, delta, delta_err
+
+
+PHASE_GROUP = 128   # samples that share the random window phase of every sub-step
+
+
+def phase_group_densities(sample_counts, L: int):
+    """Densities of each 128-sample phase group at every record: the independent replicas of
+    one run.  Samples of a phase group share the window phase of every sub-step and so are
+    correlated; distinct phase groups are independent, so error bars take batch means over
+    them (feed the result to jackknife_effective_exponent).
+
+    sample_counts: [R][S] occupied sites per sample at R records (S a multiple of 128).
+    Returns [S/128][R] densities."""
+    c = np.asarray(sample_counts, dtype=np.float64)
+    if c.ndim != 2 or c.shape[1] % PHASE_GROUP:
+        raise ValueError("need [records][samples] counts with samples a multiple of 128")
+    R, S = c.shape
+    return c.reshape(R, S // PHASE_GROUP, PHASE_GROUP).sum(axis=2).T / (PHASE_GROUP * float(L))

@@ -1,5 +1,6 @@
 """Pins of the effective-exponent post-processing (Sec. 5.3) on exact power laws."""
 import numpy as np
+import pytest
 
 from paper_1301_6082_gb300.analysis import effective_exponent
 from paper_1301_6082_gb300.workloads import log_times
@@ -53,3 +54,34 @@ def test_jackknife_identical_replicas_have_zero_error():
     mean, err, _, de, de_err = jackknife_effective_exponent(t, reps)
     assert np.all(err < 1e-15) and np.all(de_err < 1e-12)
     np.testing.assert_allclose(de, 0.5, rtol=1e-12)
+
+
+def test_phase_group_densities_group_and_normalise():
+    from paper_1301_6082_gb300.analysis import phase_group_densities
+    rng = np.random.default_rng(3)
+    L, R, S = 1000, 5, 512
+    counts = rng.integers(0, L + 1, size=(R, S))
+    g = phase_group_densities(counts, L)
+    assert g.shape == (S // 128, R)
+    for h in range(S // 128):
+        np.testing.assert_allclose(g[h], counts[:, 128 * h:128 * (h + 1)].sum(1) / (128 * L))
+    # the mean over phase groups is the run's density
+    np.testing.assert_allclose(g.mean(0), counts.sum(1) / (S * L))
+    with pytest.raises(ValueError):
+        phase_group_densities(counts[:, :100], L)
+
+
+def test_phase_group_error_bars_through_the_jackknife():
+    """Independent phase groups with a known spread: the jackknife error of the mean density
+    is the textbook standard error over groups."""
+    from paper_1301_6082_gb300.analysis import jackknife_effective_exponent, phase_group_densities
+    rng = np.random.default_rng(9)
+    L, S = 4096, 128 * 16
+    t = np.array([1.0, 2.0, 4.0, 8.0])
+    base = 0.5 * t ** -0.3
+    counts = np.stack([rng.binomial(L, b, size=S) for b in base])
+    g = phase_group_densities(counts, L)
+    mean, err, _, delta, derr = jackknife_effective_exponent(t, g)
+    np.testing.assert_allclose(mean, counts.sum(1) / (S * L))
+    np.testing.assert_allclose(err, g.std(0, ddof=1) / np.sqrt(g.shape[0]), rtol=1e-12)
+    assert np.all(np.abs(delta - 0.3) < 6 * derr + 1e-3)
