@@ -474,6 +474,7 @@ int make_plan(pcpd_t *h, const pcpd_params *prm, bool paired = false) {
   if (per_sm < 1) return fail(PCPD_EINVAL, "tile plan does not fit one CTA per SM");
   h->grid = per_sm * sms;
   const uint64_t tiles = (uint64_t)(h->G / h->gpi) * h->n_seg;
+  if (paired && !h->ring && tiles >= (1ull << 24)) return make_plan(h, prm, false);   // longer tiles
   if (tiles >= (1ull << 24))   // a work item carries the tile index in 24 bits
     return fail(PCPD_EINVAL, "%llu tiles per epoch (at most 2^24 - 1): fewer samples or longer tiles",
                 (unsigned long long)tiles);
