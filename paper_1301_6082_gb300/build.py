@@ -78,6 +78,22 @@ def build(force: bool = False, verbose: bool = False, debug: bool = False) -> st
     return out
 
 
+PIPES_LIB = os.path.join(HERE, "libpcpd_pipes.so")
+PIPES_SRC = os.path.join(CSRC, "pcpd_pipes.cu")
+PIPES_DEPS = [PIPES_SRC, os.path.join(os.path.dirname(HERE), "include", "pcpd_pipes.h")]
+
+
+def build_pipes(force: bool = False) -> str:
+    """libpcpd_pipes.so: the integer-pipe lane-rate kernels behind the roofline peaks."""
+    stale = force or not os.path.exists(PIPES_LIB) or any(
+        os.path.getmtime(d) > os.path.getmtime(PIPES_LIB) for d in PIPES_DEPS)
+    if stale:
+        tmp = PIPES_LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call([nvcc(), *flags(), PIPES_SRC, "-o", tmp, "-lcudart"])
+        os.replace(tmp, PIPES_LIB)
+    return PIPES_LIB
+
+
 EXAMPLE_SRC = os.path.join(HERE, "examples", "pcpd_decay.c")
 EXAMPLE_BIN = os.path.join(HERE, "examples", "pcpd_decay")
 
@@ -97,3 +113,4 @@ def build_example(force: bool = False) -> str:
 
 if __name__ == "__main__":
     build(force=True, verbose=True)
+    build_pipes(force=True)

@@ -18,14 +18,15 @@ def lib():
     return pcpd.load()
 
 
-def declared_functions():
-    names = []
-    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
-        if fn.endswith(".h"):
-            src = open(os.path.join(ROOT, "include", fn)).read()
-            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-            names += re.findall(r"\b(pcpd_\w+)\s*\(", src)
-    return sorted(set(names))
+def declared_functions(header: str = "pcpd.h"):
+    src = open(os.path.join(ROOT, "include", header)).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pcpd_\w+)\s*\(", src)))
+
+
+def test_every_header_is_checked():
+    assert sorted(f for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h")) == \
+        ["pcpd.h", "pcpd_pipes.h"]
 
 
 def test_every_declared_symbol_is_exported(lib):
@@ -39,6 +40,17 @@ def test_binding_covers_header():
     from paper_1301_6082_gb300 import pcpd
     bound = {n for n, _, _ in pcpd.SIGNATURES}
     assert set(declared_functions()) <= bound
+
+
+def test_pipe_rate_library_exports_its_header():
+    from paper_1301_6082_gb300 import build, pipes
+    build.build_pipes()
+    plib = pipes.load()
+    names = declared_functions("pcpd_pipes.h")
+    assert names == ["pcpd_pipe_count", "pcpd_pipe_rate"]
+    for n in names:
+        assert hasattr(plib, n), n
+    assert plib.pcpd_pipe_count() == len(pipes.OPS)
 
 
 def test_thresholds_match_oracle(lib, oracle_mod):
