@@ -91,8 +91,10 @@ pcpd_t *pcpd_create(uint32_t L, uint32_t samples, double p, double d, uint64_t s
 int pcpd_create_ex(const pcpd_params *prm, pcpd_t **out);
 
 /* Advance every sample by steps_mcs Monte Carlo steps (t_now -> t_now + steps_mcs) and
- * record the occupation at each MCS time in record_times_mcs[0..n_times): strictly
- * increasing, each in (t_now, t_now + steps_mcs]; a time equal to t_now is allowed only as
+ * record the occupation at each MCS time in record_times_mcs[0..n_times).  Time unit: Alg. 1
+ * (Sec. 2) advances time by 1/L per attempted update, so one MCS is L attempts per sample;
+ * with K windows per sub-step, MCS time t is reached after ceil(t*L/K) sub-steps.  Times
+ * strictly increasing, each in (t_now, t_now + steps_mcs]; a time equal to t_now is allowed only as
  * the first entry and records the current state.  Work is enqueued on the handle's stream;
  * the call returns without waiting for it.  n_times may be 0 (record_times_mcs may then be
  * NULL).  Errors: PCPD_EINVAL (times out of order or range, sub-step count >= 2^32),
@@ -102,9 +104,10 @@ int pcpd_run(pcpd_t *h, uint64_t steps_mcs, const uint64_t *record_times_mcs, si
 /* Number of records taken so far (all pcpd_run calls). */
 size_t pcpd_num_records(const pcpd_t *h);
 
-/* Copy the first n_times records (waits for the handle's stream): rho_out[r] =
- * counts[r] / (L * samples) (nullable), counts_out[r] = occupied (site, sample) pairs (nullable),
- * times_out[r] = the record's MCS time (nullable).  PCPD_EINVAL if n_times exceeds
+/* Copy the first n_times records (waits for the handle's stream): the particle density
+ * rho(t) whose decay the paper analyses (Sec. 5.3), rho_out[r] = counts[r] / (L * samples)
+ * (nullable), counts_out[r] = occupied (site, sample) pairs (nullable); pcpd_record_times:
+ * times_out[r] = the record's MCS time.  PCPD_EINVAL if n_times exceeds
  * pcpd_num_records(). */
 int pcpd_density(const pcpd_t *h, double *rho_out, uint64_t *counts_out, size_t n_times);
 int pcpd_record_times(const pcpd_t *h, uint64_t *times_out, size_t n_times);
@@ -114,11 +117,18 @@ int pcpd_record_times(const pcpd_t *h, uint64_t *times_out, size_t n_times);
  * the particle density (Sec. 5.3).  Waits. */
 int pcpd_pair_counts(const pcpd_t *h, uint64_t *counts_out, size_t n_times);
 
+/* The pair density itself (Sec. 5.3): rho_pair_out[r] = pair counts[r] / (L * samples) for the
+ * first n_times records.  Waits.  PCPD_EINVAL if n_times exceeds pcpd_num_records(). */
+int pcpd_pair_density(const pcpd_t *h, double *rho_pair_out, size_t n_times);
+
 /* Per-sample counts of record r into out[samples] (uint32, sample order 0..samples-1).
  * Needs per_sample at creation; else PCPD_ESTATE. */
 int pcpd_sample_counts(const pcpd_t *h, size_t r, uint32_t *out);
 
-/* Copy the current lattice to host memory in the canonical layout (G*L words).  Waits. */
+/* Checkpoint and resume.  The paper is silent on both; resuming is exact here because every
+ * random word is addressed by (seed, window, sub-step, group, block), so the state of a run is
+ * just its lattice and its sub-step counter.
+ * Copy the current lattice to host memory in the canonical layout (G*L words).  Waits. */
 int pcpd_get_lattice(const pcpd_t *h, uint32_t *host_out);
 
 /* Replace the lattice by host_in (canonical layout) and set the clock to `substep` completed
@@ -407,13 +417,17 @@ void pcpd_paper_destroy(pcpd_paper_t *h);
  *   lat_out  device, same layout, not overlapping lat_in: receives the state after
  *            substep_begin + n_substeps sub-steps (bit-identical to pcpd_run_substeps).
  *   L, samples, p, d, seed   as for pcpd_create; stream: cudaStream_t or NULL.
- * The call waits for the work to finish.  Errors: PCPD_EINVAL (bad sizes or pointers, or more
+ * The call is synchronous: it waits on `stream` after every launch to read the error word
+ * into host memory, so it cannot be made while `stream` (or the legacy default stream) is
+ * being captured into a CUDA graph.  Errors: PCPD_EINVAL (bad sizes or pointers, or more
  * tiles per epoch than the scratch holds -- about 16384 columns of up to ~50k sites, fewer
- * for longer columns), PCPD_ENODEV, PCPD_ECUDA, PCPD_ETIMEOUT.
+ * for longer columns), PCPD_ENODEV, PCPD_ECUDA, PCPD_ETIMEOUT.  After any error the contents
+ * of both lattices are undefined (a run may stop between two launches, with the newest state
+ * in either buffer).
  * Every call shares the one scratch array and clears it first; calls that overlap on the GPU
- * (from several threads or streams at once) race on it and must not be made.  The first call
- * on a device looks up the array's device address (cudaGetSymbolAddress); make that first
- * call before any stream capture. */
+ * (from several threads or streams at once) race on it and must not be made.  Every call
+ * looks up the array's device address on the current device (cudaGetSymbolAddress, which
+ * allocates nothing), so the call stays valid after a cudaDeviceReset. */
 int pcpd_sweep_noalloc(uint32_t *lat_in, uint32_t *lat_out, uint32_t L, uint32_t samples, double p,
                        double d, uint64_t seed, uint64_t substep_begin, uint64_t n_substeps,
                        void *stream);

@@ -954,6 +954,16 @@ int pcpd_pair_counts(const pcpd_t *h, uint64_t *counts_out, size_t n) {
   return PCPD_OK;
 }
 
+int pcpd_pair_density(const pcpd_t *h, double *rho_pair_out, size_t n) {
+  if (!h || (n && !rho_pair_out)) return fail(PCPD_EINVAL, "NULL argument");
+  std::vector<uint64_t> c(n);
+  const int rc = pcpd_pair_counts(h, c.data(), n);
+  if (rc) return rc;
+  const double norm = (double)h->L * (double)h->S;
+  for (size_t i = 0; i < n; ++i) rho_pair_out[i] = (double)c[i] / norm;
+  return PCPD_OK;
+}
+
 int pcpd_sample_counts(const pcpd_t *h, size_t r, uint32_t *out) {
   if (!h || !out) return fail(PCPD_EINVAL, "NULL argument");
   if (!h->per_sample) return fail(PCPD_ESTATE, "per-sample counts were not requested at creation");
@@ -1042,24 +1052,17 @@ constexpr uint32_t kNoAllocMaxTiles = 16384;   // tiles per epoch the array can 
 constexpr size_t kNoAllocScratchWords = kNoAllocMaxTiles + 64;
 static __device__ __align__(256) uint32_t g_noalloc_scratch[kNoAllocScratchWords];
 
-constexpr int kNoAllocMaxDevices = 64;
-std::mutex g_noalloc_mu;
-uint32_t *g_noalloc_ptr[kNoAllocMaxDevices] = {};
-
-// Device address of the scratch array on the current device (looked up once per device).
+// Device address of the scratch array on the current device.  In host code the array's name
+// is only a host-side stand-in; the address is looked up on every call (cheap, allocates
+// nothing), so a context re-created after cudaDeviceReset gets its own.
 int noalloc_scratch(uint32_t **out) {
   int dev = 0;
   CU(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(PCPD_ENODEV, "device index %d out of range", dev);
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
-    void *p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p)
-      return fail(PCPD_ECUDA, "cudaGetSymbolAddress(scratch) on device %d: %s", dev, cudaGetErrorString(e));
-    g_noalloc_ptr[dev] = (uint32_t *)p;
-  }
-  *out = g_noalloc_ptr[dev];
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p)
+    return fail(PCPD_ECUDA, "cudaGetSymbolAddress(scratch) on device %d: %s", dev, cudaGetErrorString(e));
+  *out = (uint32_t *)p;
   return PCPD_OK;
 }
 

@@ -71,6 +71,7 @@ SIGNATURES = [
     ("pcpd_record_times", C.c_int, [C.c_void_p, _u64p, C.c_size_t]),
     ("pcpd_sample_counts", C.c_int, [C.c_void_p, C.c_size_t, _u32p]),
     ("pcpd_pair_counts", C.c_int, [C.c_void_p, _u64p, C.c_size_t]),
+    ("pcpd_pair_density", C.c_int, [C.c_void_p, _f64p, C.c_size_t]),
     ("pcpd_get_lattice", C.c_int, [C.c_void_p, _u32p]),
     ("pcpd_set_lattice", C.c_int, [C.c_void_p, _u32p, C.c_uint64]),
     ("pcpd_get_lattice_async", C.c_int, [C.c_void_p, _u32p]),
@@ -247,7 +248,12 @@ class Pcpd:
         return c
 
     def pair_density(self) -> np.ndarray:
-        return self.pair_counts() / float(self.L * self.S)
+        """Occupied nearest-neighbour pairs per site and sample, per record (Sec. 5.3)."""
+        n = self.num_records
+        r = np.zeros(n, dtype=np.float64)
+        if n:
+            _check(load().pcpd_pair_density(self._h, _ptr(r, C.c_double), n))
+        return r
 
     def density(self) -> np.ndarray:
         n = self.num_records
@@ -466,11 +472,33 @@ def dev_rate_masks(words_dev, t_d: int, t_da: int, masks_dev, n: int, stream=Non
                                       C.c_void_p(masks_dev.data_ptr()), n, s))
 
 
+def check_noalloc_buffers(lat_in_dev, lat_out_dev, L: int, samples: int):
+    """The C entry point cannot see how large the caller's buffers are: refuse, before any
+    launch, buffers that are not contiguous CUDA tensors on the current device holding at
+    least (samples/32)*L uint32 words each."""
+    need = (samples // 32) * L * 4
+    bufs = (("lat_in", lat_in_dev), ("lat_out", lat_out_dev))
+    for name, t in bufs:
+        if not getattr(t, "is_cuda", False):
+            raise PcpdError(PCPD_EINVAL, f"{name} must be a CUDA tensor")
+        if not t.is_contiguous():
+            raise PcpdError(PCPD_EINVAL, f"{name} must be contiguous")
+        have = t.numel() * t.element_size()
+        if have < need:
+            raise PcpdError(PCPD_EINVAL, f"{name} holds {have} bytes, the lattice needs {need}")
+    import torch
+    cur = torch.cuda.current_device()
+    for name, t in bufs:
+        if t.device.index != cur:
+            raise PcpdError(PCPD_EINVAL, f"{name} is on cuda:{t.device.index}, the current device is cuda:{cur}")
+
+
 def sweep_noalloc(lat_in_dev, lat_out_dev, L: int, samples: int, p: float, d: float, seed: int,
                   substep_begin: int, n_substeps: int, stream=None):
     """Allocation-free sweep on caller-owned device lattices (torch CUDA tensors or objects
     with data_ptr()): lat_out receives the state after n_substeps more sub-steps; lat_in is
     used as work space.  For callers that cannot let the library allocate device memory."""
+    check_noalloc_buffers(lat_in_dev, lat_out_dev, L, samples)
     s = C.c_void_p(int(getattr(stream, "cuda_stream", 0) or 0)) if stream is not None else None
     _check(load().pcpd_sweep_noalloc(C.c_void_p(lat_in_dev.data_ptr()), C.c_void_p(lat_out_dev.data_ptr()),
                                      L, samples, p, d, seed, substep_begin, n_substeps, s))

@@ -180,3 +180,44 @@ def test_oracle_does_not_use_the_product():
     for f in os.listdir(odir):
         if f.endswith((".py", ".c", ".h")):
             assert not pat.search(open(os.path.join(odir, f)).read()), f
+
+
+class _FakeCudaTensor:
+    """Stands in for a CUDA tensor: the allocation-free sweep's binding must refuse a buffer
+    by its size before any device call."""
+    is_cuda = True
+
+    def __init__(self, words, contiguous=True):
+        self.words, self.contig = words, contiguous
+
+    def is_contiguous(self):
+        return self.contig
+
+    def numel(self):
+        return self.words
+
+    def element_size(self):
+        return 4
+
+    def data_ptr(self):
+        raise AssertionError("the binding reached the device call")
+
+
+def test_noalloc_binding_refuses_bad_buffers_before_any_launch():
+    import torch
+    from paper_1301_6082_gb300 import pcpd
+    L, S = 1001, 64
+    ok = _FakeCudaTensor((S // 32) * L)
+    with pytest.raises(pcpd.PcpdError) as e:
+        pcpd.sweep_noalloc(_FakeCudaTensor((S // 32) * L - 1), ok, L, S, 0.1, 0.5, 1, 0, 5)
+    assert e.value.code == pcpd.PCPD_EINVAL and "lat_in" in str(e.value)
+    with pytest.raises(pcpd.PcpdError) as e:
+        pcpd.sweep_noalloc(ok, _FakeCudaTensor(10), L, S, 0.1, 0.5, 1, 0, 5)
+    assert "lat_out" in str(e.value)
+    with pytest.raises(pcpd.PcpdError) as e:
+        pcpd.sweep_noalloc(_FakeCudaTensor((S // 32) * L, contiguous=False), ok, L, S, 0.1, 0.5, 1, 0, 5)
+    assert "contiguous" in str(e.value)
+    cpu = torch.zeros((S // 32) * L, dtype=torch.int32)
+    with pytest.raises(pcpd.PcpdError) as e:
+        pcpd.sweep_noalloc(cpu, ok, L, S, 0.1, 0.5, 1, 0, 5)
+    assert "CUDA" in str(e.value)

@@ -25,7 +25,11 @@ def P():
 
 
 @pytest.mark.parametrize("L,S,p,d,n1,n2", [
-    (1000, 64, 0.15, 0.5, 37, 90),          # whole-ring tiles, L not a multiple of 4
+    # this entry point keeps the caller's unpadded layout (column pitch = L): with L % 4 != 0
+    # and several columns, later columns start off a 16-byte boundary and take the plain-load
+    # path instead of the bulk copy
+    (1001, 64, 0.15, 0.5, 37, 90),          # whole-ring tiles, 2 columns, 1001 = 4*250 + 1
+    (65538, 96, 0.2, 0.3, 70, 200),         # segmented tiles, 3 columns, 65538 = 4*16384 + 2
     (65536, 256, 0.11, 0.1, 130, 260),      # segmented tiles across several epochs
 ])
 def test_noalloc_matches_allocating_path_twice(P, L, S, p, d, n1, n2):
