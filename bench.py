@@ -12,8 +12,10 @@ Metric: attempted site updates per second (sample x window attempts; S*K per sub
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-N > 1 (torchrun): independent replicas, one per GPU, with disjoint seeds; no data-path
-collective (the runs do not exchange anything); value = all ranks' attempts / max time.
+N > 1 (torchrun): weak scaling by group range -- rank r runs the 4096 samples (128 groups)
+[128r, 128r + 128) of one ensemble of 4096*N samples per run (pcpd_params.group0), so the
+ranks together reproduce the one-GPU run of that ensemble bit for bit; no data-path
+collective (the shards exchange nothing); value = all ranks' attempts / max time.
 """
 from __future__ import annotations
 
@@ -28,7 +30,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_1301_6082_gb300.replicas import combine, replica_seed  # noqa: E402
+from paper_1301_6082_gb300.replicas import combine, weak_shard  # noqa: E402
 from paper_1301_6082_gb300.workloads import SMEM_L65536, batch_instances, log_times, request_stream  # noqa: E402
 
 METRIC = "attempted site updates/s"
@@ -155,24 +157,35 @@ def dist_env():
     return world, rank, local
 
 
-def run_cpu_sample(budget_groups: int = 16, substeps: int = 300):
-    """The oracle as it stands, on a bounded sample of the workload: `budget_groups` groups
-    (32 samples each) of the L=65536 lattice at (d,p) = (0.5, 0.15), `substeps` sub-steps from
-    the full start, threads = min(host cores, groups)."""
+def host_cores() -> int:
+    """Cores this process may run on (its CPU affinity), else the machine's count."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_cpu_sample(budget_groups: int | None = None, substeps: int = 300):
+    """The oracle as it stands, on a bounded sample of the workload: one 32-sample group per
+    host core the process may run on (at least 16 groups) of the L=65536 lattice at (d,p) =
+    (0.5, 0.15), `substeps` sub-steps from the full start, one oracle thread per core (the
+    oracle splits its work by group)."""
     from oracle import oracle as O
     L = SMEM_L65536["L"]
-    S = 32 * budget_groups
+    avail = host_cores()
+    groups = budget_groups or max(16, avail)
+    S = 32 * groups
     d, p = 0.5, 0.15
-    cores = min(os.cpu_count() or 1, budget_groups)
+    cores = min(avail, groups)
     st = O.init_state(L, S, O.MODE_FULL, 1)
     t0 = time.perf_counter()
     O.run(st, p, d, 1, 0, substeps, threads=cores)
     dt = time.perf_counter() - t0
     attempts = S * (L // 3) * substeps
-    return {"value": attempts / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+    return {"value": attempts / dt, "unit": UNIT, "cores": cores, "host_cores": avail, "kind": "oracle",
             "value_per_core": attempts / dt / cores,
-            "sample": f"{budget_groups} groups ({S} samples) of L={L}, d=0.5 p=0.15, {substeps} sub-steps "
-                      f"from full ({attempts:.3e} attempts, {dt:.1f} s)"}
+            "sample": f"{groups} groups ({S} samples) of L={L}, d=0.5 p=0.15, {substeps} sub-steps "
+                      f"from full ({attempts:.3e} attempts, {dt:.1f} s, {cores} threads on {avail} cores)"}
 
 
 def run_rs_sample(samples: int = 256, mcs: int = 40):
@@ -181,7 +194,7 @@ def run_rs_sample(samples: int = 256, mcs: int = 40):
     paper's simple-CPU-program figure."""
     from oracle import oracle as O
     L = SMEM_L65536["L"]
-    cores = min(os.cpu_count() or 1, samples)
+    cores = min(host_cores(), samples)
     st = O.init_state(L, samples, O.MODE_FULL, 1)
     t0 = time.perf_counter()
     O.rs_run(st, 0.15, 0.5, 1, 0, mcs * L, threads=cores)
@@ -411,7 +424,7 @@ def reference_arm(args, world, rank):
     """The oracle timed on the host cores, one bounded sample of the workload per step."""
     if rank != 0:
         return 0
-    groups, subs = 8, 60
+    groups, subs = host_cores(), 60   # one 32-sample group per host core, all cores busy
     res = None
     times = []
     for i in range(args.warmup + args.steps):
@@ -428,7 +441,8 @@ def reference_arm(args, world, rank):
             "data": "synthetic",
             "config": {"workload": SMEM_L65536["name"], "L": SMEM_L65536["L"], "samples": SMEM_L65536["S"],
                        "note": "each step: the CPU oracle on a bounded sample of the workload"},
-            "cpu_baseline": {"kind": "oracle", "cores": res["cores"], "sample": res["sample"], "value": value,
+            "cpu_baseline": {"kind": "oracle", "cores": res["cores"], "host_cores": res["host_cores"],
+                             "sample": res["sample"], "value": value,
                              "unit": UNIT, "value_per_core": value / res["cores"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -493,9 +507,10 @@ def main():
     # the three runs are independent: one stream each, so one launch's tail overlaps the next
     streams = [torch.cuda.Stream() for _ in runs]
     main_stream = torch.cuda.Stream()
+    g0, _ = weak_shard(S // 32, rank)   # this rank's groups of the 4096*world-sample ensemble
     sims = []
     for i, (d, p) in enumerate(runs):
-        sims.append(pcpd.Pcpd(L, S, p, d, seed=replica_seed(W["seed"], rank), stream=streams[i]))
+        sims.append(pcpd.Pcpd(L, S, p, d, seed=W["seed"], stream=streams[i], group0=g0))
     ops_item = []
     for d, p in runs:
         td, tda = pcpd.thresholds(p, d)
@@ -577,7 +592,7 @@ def main():
     if args.e2e_steps > 0:
         host = [torch.empty((S // 32, L), dtype=torch.int32, pin_memory=True) for _ in sims]
         streams = [torch.cuda.Stream() for _ in sims]
-        esims = [pcpd.Pcpd(L, S, p, d, seed=replica_seed(W["seed"], rank), stream=st)
+        esims = [pcpd.Pcpd(L, S, p, d, seed=W["seed"], stream=st, group0=g0)
                  for (d, p), st in zip(runs, streams)]
         for es, s, hb in zip(esims, sims, host):
             arr = hb.numpy().view(np.uint32)
@@ -639,7 +654,7 @@ def main():
                            "(consecutive segments of the 1e6-MCS runs, records included)",
                            "records": W["n_rec"], "seed": W["seed"], "init": "full",
                            "l2": "inputs larger than L2: 3 lattices x 2 buffers x 32 MiB = 192 MiB, streamed per tile epoch",
-                           "parallelism": f"replicas x{world}"},
+                           "parallelism": f"group shards x{world} (rank r: groups [128r, 128r+128) of one ensemble)"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": launches, "batch": batch, "serving": serving, "streamed": streamed, "paper_scheme": paper, "tuples": tuples,
                 "paper_context": dict(PAPER_CONTEXT, this_run_over_paper_gpu=value / PAPER_CONTEXT["gpu_moves_per_s"])}

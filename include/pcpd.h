@@ -79,6 +79,15 @@ typedef struct pcpd_params {
                                 3 = TCPD (triplets), 4 = QCPD (quadruplets); windows of n+1
                                 sites, K = floor(L/(n+1)) per sub-step, annihilation empties
                                 the n-tuple (see pcpd_substep_of_time_n) */
+    uint32_t group0;         /* first 32-sample group of this instance inside a larger
+                                ensemble of the same seed and rates: the instance holds
+                                groups group0 .. group0 + samples/32 - 1 and draws exactly
+                                the random numbers those groups draw in a run of the whole
+                                ensemble, so instances that split one ensemble's groups
+                                between them (e.g. one per GPU; the paper runs one system
+                                per workgroup, Sec. 3) together reproduce that run bit for
+                                bit.  A multiple of 4 (whole 128-sample phase groups), with
+                                group0 + samples/32 <= 2^26; 0 = a standalone instance. */
 } pcpd_params;
 
 /* Create a simulation of `samples` PCPD samples on a ring of L sites, initialised fully

@@ -174,6 +174,7 @@ constexpr size_t kStaticSmem = sizeof(uint32_t) * pcpdk::kPhiChunk + 34 * sizeof
 struct pcpd {
   uint32_t L = 0, K = 0, S = 0, G = 0, pitch = 0;
   uint32_t W = 3;             // window width: tuple size + 1
+  uint32_t g_base = 0;        // global index of the first group (pcpd_params.group0)
   double p = 0, d = 0;
   uint64_t seed = 0, td = 0, tda = 0;
   pcpdk::Thresholds T{};
@@ -548,6 +549,7 @@ void fill_desc(const pcpd_t *h, pcpdk::InstDesc &D, uint64_t n_begin, uint64_t n
   D.L = h->L;
   D.K = h->K;
   D.W = h->W;
+  D.g_base = h->g_base;
   D.G = h->G;
   D.S = h->S;
   D.pitch = h->pitch;
@@ -607,6 +609,7 @@ int launch_sweep(pcpd_t *h, uint64_t n_end, const std::vector<uint64_t> &subs, s
     D.L = h->L;
     D.K = h->K;
     D.W = h->W;
+    D.g_base = h->g_base;
     D.G = h->G;
     D.S = h->S;
     D.pitch = h->pitch;
@@ -711,6 +714,8 @@ int create_handle(const pcpd_params *prm, pcpd_t **out, bool batch_member) {
   if (prm->init < 0 || prm->init > 2) return fail(PCPD_EINVAL, "unknown init mode %d", prm->init);
   if (prm->tuple == 1u || prm->tuple > 4u) return fail(PCPD_EINVAL, "tuple must be 0 or 2 (PCPD), 3 (TCPD) or 4 (QCPD) (tuple=%u)", prm->tuple);
   if (prm->L < (prm->tuple ? prm->tuple : 2u) + 1u) return fail(PCPD_EINVAL, "L=%u is shorter than one window", prm->L);
+  if (prm->group0 % 4u || (uint64_t)prm->group0 + prm->samples / 32u > (1ull << 26))
+    return fail(PCPD_EINVAL, "group0 must be a multiple of 4 with group0 + samples/32 <= 2^26 (group0=%u)", prm->group0);
   uint64_t td, tda;
   int rc = thresholds(prm->p, prm->d, &td, &tda);
   if (rc) return rc;
@@ -726,6 +731,7 @@ int create_handle(const pcpd_params *prm, pcpd_t **out, bool batch_member) {
   pcpd_t *h = new pcpd();
   h->L = prm->L;
   h->W = (prm->tuple ? prm->tuple : 2u) + 1u;
+  h->g_base = prm->group0;
   h->K = prm->L / h->W;
   h->S = prm->samples;
   h->G = prm->samples / 32u;
@@ -771,7 +777,7 @@ int create_handle(const pcpd_params *prm, pcpd_t **out, bool batch_member) {
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_done, 0, (h->tiles + 2) * sizeof(uint32_t), h->stream);
     if (e != cudaSuccess) return bail(fail(PCPD_ENOMEM, "engine scratch: %s", cudaGetErrorString(e)));
   }
-  pcpdk::k_init<<<1024, 256, 0, h->stream>>>(h->buf[0], h->L, h->pitch, h->G, h->init, h->k0, h->k1);
+  pcpdk::k_init<<<1024, 256, 0, h->stream>>>(h->buf[0], h->L, h->pitch, h->G, h->init, h->k0, h->k1, h->g_base);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return bail(fail(PCPD_ECUDA, "init launch: %s", cudaGetErrorString(e)));
   g_launches.fetch_add(1, std::memory_order_relaxed);

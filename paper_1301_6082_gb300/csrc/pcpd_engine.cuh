@@ -46,6 +46,7 @@ struct InstDesc {
   uint32_t n_begin, n_end;   // sub-steps of this launch
   uint32_t n_rec;            // records in (n_begin, n_end]
   uint32_t W;                // window width: tuple size + 1 (3 PCPD, 4 TCPD, 5 QCPD)
+  uint32_t g_base;           // global index of the instance's first group (a multiple of 4)
   uint32_t *buf0, *buf1;     // state at n_begin is in buf0
   const uint32_t *rec_sub;   // [n_rec] sub-step of each record (increasing)
   unsigned long long *rec_total;  // [n_rec]
@@ -151,7 +152,7 @@ __device__ __forceinline__ void run_item(const InstDesc &D, uint32_t *smem, uint
   const uint32_t tile_len = core_len + 2u * H;
   const uint32_t win_lim = RING ? L : tile_len;   // a window's sites index its column's region
   const uint32_t base = RING ? 0u : (uint32_t)(((uint64_t)s0 + L - H) % L);
-  const uint32_t h = (32u * g0) / 128u;   // one phase group for all gpi columns
+  const uint32_t h = (D.g_base + g0) >> 2;   // one 128-sample phase group for all gpi columns
   const uint32_t n_a = D.n_begin + e * D.tau;   // < n_end < 2^32
   // the epoch's end in 64 bits: n_a + tau may pass 2^32 near the end of the counter range
   const uint32_t n_b = (uint32_t)min((unsigned long long)n_a + D.tau, (unsigned long long)D.n_end);
@@ -214,7 +215,7 @@ __device__ __forceinline__ void run_item(const InstDesc &D, uint32_t *smem, uint
       uint32_t k = 0, idx[W] = {};
       const bool valid = i < n_cand && candidate<RING, W>(G, ii, L, K, k, idx);
       uint32_t *sm = smem + col * L;
-      const uint32_t g = g0 + col;
+      const uint32_t g = D.g_base + g0 + col;   // the group's index in the Philox counter
       Cmp cD = cmp_init(D.T.td, D.T.td_full), cA = cmp_init(D.T.tda, D.T.tda_full);
       uint32_t O;
       {
@@ -264,7 +265,7 @@ __device__ __forceinline__ void run_item(const InstDesc &D, uint32_t *smem, uint
       }
       uint32_t k = 0, idx[W] = {};
       candidate<RING, W>(G, ii, L, K, k, idx);
-      finish_from3(k, n, g0 + col, rk, D.T, cD, cA);
+      finish_from3(k, n, D.g_base + g0 + col, rk, D.T, cD, cA);
       apply_window<W>(smem + col * L, idx, O, cD.lt, cA.lt, win_lim);
     }
     if (!RING) {

@@ -384,9 +384,9 @@ __device__ __forceinline__ void apply_window(uint32_t *sm, const uint32_t (&idx)
 }
 
 // Initial lattice: mode 0 full, 1 empty, 2 i.i.d. Bernoulli(1/2) bits (Philox tag INIT,
-// counter (i, 0, g, INIT<<28), first word).
+// counter (i, 0, g_base + g, INIT<<28), first word; g_base = the instance's first group).
 __global__ void k_init(uint32_t *lat, uint32_t L, uint32_t pitch, uint32_t G, int mode, uint32_t k0,
-                       uint32_t k1) {
+                       uint32_t k1, uint32_t g_base) {
   const size_t total = (size_t)G * L;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
        idx += (size_t)gridDim.x * blockDim.x) {
@@ -395,7 +395,7 @@ __global__ void k_init(uint32_t *lat, uint32_t L, uint32_t pitch, uint32_t G, in
     if (mode == 0) v = 0xFFFFFFFFu;
     else if (mode == 1) v = 0u;
     else {
-      uint32_t x0 = i, x1 = 0u, x2 = g, x3 = kTagInit << 28;
+      uint32_t x0 = i, x1 = 0u, x2 = g_base + g, x3 = kTagInit << 28;
       philox4x32_10(x0, x1, x2, x3, k0, k1);
       v = x0;
     }

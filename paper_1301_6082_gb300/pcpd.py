@@ -34,7 +34,7 @@ class Params(C.Structure):
                 ("seed", C.c_uint64), ("init", C.c_int), ("stream", C.c_void_p),
                 ("dev_lattice", C.c_void_p), ("dev_bytes", C.c_size_t), ("per_sample", C.c_int),
                 ("plan_threads", C.c_uint32), ("plan_seg_sites", C.c_uint32), ("plan_tau", C.c_uint32),
-                ("autotune", C.c_int), ("jit", C.c_int), ("tuple", C.c_uint32)]
+                ("autotune", C.c_int), ("jit", C.c_int), ("tuple", C.c_uint32), ("group0", C.c_uint32)]
 
 
 class PlanInfo(C.Structure):
@@ -174,7 +174,8 @@ class Pcpd:
     def __init__(self, L: int, samples: int, p: float, d: float, seed: int = 1,
                  init: int = INIT_FULL, per_sample: bool = False, stream=None,
                  dev_lattice=None, plan_threads: int = 0, plan_seg_sites: int = 0,
-                 plan_tau: int = 0, autotune: bool = False, jit: int = 0, tuple_n: int = 2):
+                 plan_tau: int = 0, autotune: bool = False, jit: int = 0, tuple_n: int = 2,
+                 group0: int = 0):
         lib = load()
         prm = Params()
         prm.L, prm.samples, prm.p, prm.d, prm.seed, prm.init = L, samples, p, d, seed, init
@@ -183,6 +184,7 @@ class Pcpd:
         prm.autotune = 1 if autotune else 0
         prm.jit = jit
         prm.tuple = tuple_n
+        prm.group0 = group0
         if stream is not None:
             prm.stream = C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
         self._keep = dev_lattice
@@ -318,11 +320,12 @@ class Batch:
 
     def add(self, L: int, samples: int, p: float, d: float, seed: int, steps_mcs: int,
             record_times=(), init: int = INIT_FULL, plan_threads: int = 0, plan_seg_sites: int = 0,
-            plan_tau: int = 0, tuple_n: int = 2) -> int:
+            plan_tau: int = 0, tuple_n: int = 2, group0: int = 0) -> int:
         prm = Params()
         prm.L, prm.samples, prm.p, prm.d, prm.seed, prm.init = L, samples, p, d, seed, init
         prm.plan_threads, prm.plan_seg_sites, prm.plan_tau = plan_threads, plan_seg_sites, plan_tau
         prm.tuple = tuple_n
+        prm.group0 = group0
         t = np.ascontiguousarray(record_times, dtype=np.uint64)
         idx = C.c_size_t()
         _check(load().pcpd_batch_add(self._h, C.byref(prm), steps_mcs, _ptr(t, C.c_uint64) if t.size else None,
@@ -386,10 +389,12 @@ class Server:
         self._meta = {}
 
     def submit(self, L: int, samples: int, p: float, d: float, seed: int, steps_mcs: int,
-               record_times=(), init: int = INIT_FULL, keep_lattice: bool = False, tuple_n: int = 2) -> int:
+               record_times=(), init: int = INIT_FULL, keep_lattice: bool = False, tuple_n: int = 2,
+               group0: int = 0) -> int:
         prm = Params()
         prm.L, prm.samples, prm.p, prm.d, prm.seed, prm.init = L, samples, p, d, seed, init
         prm.tuple = tuple_n
+        prm.group0 = group0
         t = np.ascontiguousarray(record_times, dtype=np.uint64)
         rid = C.c_uint64()
         _check(load().pcpd_server_submit(self._h, C.byref(prm), steps_mcs, _ptr(t, C.c_uint64) if t.size else None,

@@ -1,15 +1,34 @@
-"""Multi-GPU replicas.  Independent PCPD systems (the paper runs one system per workgroup,
-Sec. 3) shard with no exchange at all: each rank simulates its own samples with its own
-seed, and the only combination is an exact integer sum of occupation counts plus, for
-timing, a maximum over ranks.  No collective touches the data path."""
+"""Multi-GPU sharding by group range.  The 32-sample groups of one ensemble are independent
+systems (the paper runs one system per workgroup, Sec. 3) whose random numbers are addressed
+by their global group index, so an ensemble splits over ranks with no exchange at all: rank r
+runs groups [group0, group0 + n) of the ensemble (pcpd_params.group0) and the ranks together
+reproduce the one-GPU run of the whole ensemble bit for bit.  The only combination is an
+exact integer sum of occupation counts plus, for timing, a maximum over ranks.  No collective
+touches the data path."""
 from __future__ import annotations
 
-SEED_STRIDE = 1_000_003
+PHASE_GROUP = 4   # 32-sample groups per 128-sample phase group (the unit a shard must respect)
 
 
-def replica_seed(base_seed: int, rank: int) -> int:
-    """Seed of rank `rank`'s replica: disjoint Philox keys for every rank."""
-    return (base_seed + SEED_STRIDE * rank) % (1 << 64)
+def shard_groups(total_groups: int, world: int, rank: int) -> tuple[int, int]:
+    """(group0, n_groups) of rank `rank`'s share of an ensemble of `total_groups` 32-sample
+    groups split over `world` ranks: contiguous runs of whole phase groups, as even as
+    possible (a rank may get none when there are fewer phase groups than ranks)."""
+    if total_groups <= 0 or world <= 0 or not 0 <= rank < world:
+        raise ValueError("need total_groups > 0 and 0 <= rank < world")
+    n_pg = -(-total_groups // PHASE_GROUP)
+    a, b = rank * n_pg // world, (rank + 1) * n_pg // world
+    g0 = PHASE_GROUP * a
+    return g0, max(0, min(PHASE_GROUP * b, total_groups) - g0)
+
+
+def weak_shard(groups_per_rank: int, rank: int) -> tuple[int, int]:
+    """(group0, n_groups) when every rank runs the same number of groups of one ensemble of
+    world * groups_per_rank groups (weak scaling): rank r holds groups
+    [r * groups_per_rank, (r + 1) * groups_per_rank)."""
+    if groups_per_rank % PHASE_GROUP:
+        raise ValueError("groups_per_rank must be a multiple of 4 (whole phase groups)")
+    return rank * groups_per_rank, groups_per_rank
 
 
 def combine(dist, sums, maxes, device="cpu"):
