@@ -1,7 +1,8 @@
 """Near-critical sweeps (Sec. 5.3): several annihilation rates p at one diffusion rate d,
 each with several independent seeds, run as one batch on the GPU; returns the particle and
-pair densities at log-spaced times and their effective exponents.  Replicas over GPUs
-follow paper_1301_6082_gb300.replicas (disjoint seeds, summed counts)."""
+pair densities at log-spaced times and their effective exponents.  Over several GPUs, each
+rank runs a group range of every (p, seed) ensemble (paper_1301_6082_gb300.replicas) and the
+ranks sum their counts exactly."""
 from __future__ import annotations
 
 import numpy as np
