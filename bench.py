@@ -390,15 +390,10 @@ def paper_leg(pcpd, mcs: int = 1000, systems: int = 3648):
                     "annihilation draws); same unit as the paper's moves/s"}
 
 
-def serving_leg(pcpd, seconds: float = 8.0, mcs_scale: float = 1 / 600, rate_hz: float = 200.0):
-    """Poisson request stream (200 req/s; L log-uniform 2^10..2^20, 64..4096 samples,
-    p in [.05,.25], d in [.1,.9], MCS log-uniform 1e3..1e5) for `seconds` instead of 60 s and
-    with every MCS count scaled by mcs_scale (declared: the stream as specified offers
-    ~7.6e14 attempts/s, hundreds of times one GPU's capacity; x 1/600 offers ~1.5e12/s, about
-    three quarters of the batched engine's capacity).  Reports throughput and
-    p50/p99 latency from submission to result."""
+def serving_run(pcpd, reqs, seconds: float):
+    """Submit `reqs` at their Poisson arrival times to a fresh server; wait for all of them.
+    Returns (throughput in attempts/s over the wall time, p50, p99 latency, stats)."""
     import numpy as np
-    reqs = request_stream(rate_hz, seconds, seed=1, mcs_scale=mcs_scale)
     sv = pcpd.Server(hbm_budget_bytes=96 << 30, max_active=128, chunk_attempts=4 << 30)
     ids = []
     t0 = time.perf_counter()
@@ -412,12 +407,36 @@ def serving_leg(pcpd, seconds: float = 8.0, mcs_scale: float = 1 / 600, rate_hz:
     lat = np.array([sv.result(i)[2] for i in ids])
     st = sv.stats()
     sv.stop()
-    return {"workload": "Poisson %g req/s for %g s, MCS x %g" % (rate_hz, seconds, mcs_scale),
-            "requests": len(reqs), "completed": int(st["completed"]),
-            "throughput": st["attempts"] / wall, "unit": UNIT,
-            "offered": sum(r["S"] * (r["L"] // 3) * pcpd.substep_of_time(r["L"], r["mcs"]) for r in reqs) / seconds,
-            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
-            "rounds": int(st["rounds"]), "busy_frac": st["busy_seconds"] / wall}
+    return st["attempts"] / wall, float(np.percentile(lat, 50)), float(np.percentile(lat, 99)), st, wall
+
+
+def serving_leg(pcpd, seconds: float = 8.0, rate_hz: float = 200.0, fractions=(0.5, 0.75, 1.0, 1.25)):
+    """Poisson request stream (200 req/s; L log-uniform 2^10..2^20, 64..4096 samples,
+    p in [.05,.25], d in [.1,.9], MCS log-uniform 1e3..1e5) for `seconds` instead of 60 s, with
+    every MCS count scaled down (declared: as specified the stream offers ~7.6e14 attempts/s,
+    hundreds of times one GPU's capacity).  First the capacity: the same requests (MCS x 1/600)
+    all submitted at once, attempts/s until the last finishes.  Then the load curve: the stream
+    with its MCS scaled so that it offers each fraction of that capacity; throughput and p50/p99
+    latency from submission to result at each point."""
+    base_scale = 1 / 600
+    base = request_stream(rate_hz, seconds, seed=1, mcs_scale=base_scale)
+    offered_base = sum(r["S"] * (r["L"] // 3) * pcpd.substep_of_time(r["L"], r["mcs"]) for r in base) / seconds
+    burst = [dict(r, arrival=0.0) for r in base]
+    capacity, _, _, _, _ = serving_run(pcpd, burst, seconds)
+    curve = []
+    for f in fractions:
+        scale = base_scale * f * capacity / offered_base
+        reqs = request_stream(rate_hz, seconds, seed=1, mcs_scale=scale)
+        offered = sum(r["S"] * (r["L"] // 3) * pcpd.substep_of_time(r["L"], r["mcs"]) for r in reqs) / seconds
+        thr, p50, p99, st, wall = serving_run(pcpd, reqs, seconds)
+        curve.append({"load": f, "offered": offered, "throughput": thr, "p50_latency_s": p50, "p99_latency_s": p99,
+                      "requests": len(reqs), "completed": int(st["completed"]), "rounds": int(st["rounds"]),
+                      "wall_s": wall, "mcs_scale": scale})
+    at = min(curve, key=lambda c: abs(c["load"] - 0.75))
+    return {"workload": "Poisson %g req/s for %g s, MCS scaled to a fraction of capacity" % (rate_hz, seconds),
+            "unit": UNIT, "capacity": capacity, "curve": curve,
+            "throughput": at["throughput"], "p50_latency_s": at["p50_latency_s"], "p99_latency_s": at["p99_latency_s"],
+            "at_load": at["load"]}
 
 
 def reference_arm(args, world, rank):
@@ -447,6 +466,22 @@ def reference_arm(args, world, rank):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def compact(d, keys):
+    """The named entries of a leg's result (None stays None)."""
+    return None if d is None else {k: d[k] for k in keys if k in d}
+
+
+def compact_roofline(r):
+    """The roofline entries the headline line carries; the notes go to the detail line."""
+    keep = ("bound", "achieved", "peak", "unit", "frac", "traffic", "binding_pipe", "frac_logic_pipe",
+            "frac_of_issue_slots", "peak_source")
+    out = {k: r[k] for k in keep if k in r}
+    for k in ("achieved", "peak", "frac", "frac_logic_pipe", "frac_of_issue_slots"):
+        if isinstance(out.get(k), float):
+            out[k] = round(out[k], 4)
+    return out
 
 
 def main():
@@ -645,19 +680,26 @@ def main():
         cpu["alg1_random_sequential"] = run_rs_sample()
 
     if rank == 0:
+        # every leg in full on an earlier line; the headline line (printed last) stays short
+        detail = {"roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "batch": batch, "serving": serving,
+                  "streamed": streamed, "paper_scheme": paper, "tuples": tuples,
+                  "paper_context": dict(PAPER_CONTEXT, this_run_over_paper_gpu=value / PAPER_CONTEXT["gpu_moves_per_s"])}
+        print(json.dumps({"bench_detail": detail}), flush=True)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-                "config": {"workload": W["name"], "L": L, "samples": S,
-                           "runs_d_p": [list(r) for r in runs], "run_mcs": W["mcs"],
-                           "mcs_per_step": mcs, "step": "each of the 3 runs advances mcs_per_step MCS "
-                           "(consecutive segments of the 1e6-MCS runs, records included)",
-                           "records": W["n_rec"], "seed": W["seed"], "init": "full",
-                           "l2": "inputs larger than L2: 3 lattices x 2 buffers x 32 MiB = 192 MiB, streamed per tile epoch",
-                           "parallelism": f"group shards x{world} (rank r: groups [128r, 128r+128) of one ensemble)"},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-                "gpu_launches": launches, "batch": batch, "serving": serving, "streamed": streamed, "paper_scheme": paper, "tuples": tuples,
-                "paper_context": dict(PAPER_CONTEXT, this_run_over_paper_gpu=value / PAPER_CONTEXT["gpu_moves_per_s"])}
+                "config": {"workload": W["name"], "L": L, "samples": S, "runs_d_p": [list(r) for r in runs],
+                           "mcs_per_step": mcs, "l2": "inputs larger than L2 (192 MiB of lattices)",
+                           "parallelism": f"group shards x{world}"},
+                "roofline": compact_roofline(roofline), "cpu_baseline": compact(cpu, ("value", "unit", "cores", "host_cores", "kind", "sample")),
+                "e2e": compact(e2e, ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step")), "clocks": clk,
+                "gpu_launches": launches,
+                "batch": compact(batch, ("speedup", "batched", "plain", "results_identical")),
+                "serving": None if serving is None else {
+                    "capacity": serving["capacity"], "p50_latency_s": serving["p50_latency_s"],
+                    "p99_latency_s": serving["p99_latency_s"], "at_load": serving["at_load"],
+                    "curve": [[c["load"], round(c["throughput"] / 1e12, 3), round(c["p50_latency_s"], 4),
+                               round(c["p99_latency_s"], 4)] for c in serving["curve"]]}}
         print(json.dumps(line), flush=True)
     for s in sims:
         s.close()

@@ -26,17 +26,25 @@ extern "C" {
 #endif
 
 enum {
-    PCPD_PIPE_LOP3 = 0,          /* lop3.b32 (three-input XOR): the logic pipe */
-    PCPD_PIPE_IMAD_LO = 1,       /* mad.lo.u32: low half of a 32x32 product plus an addend */
-    PCPD_PIPE_IMAD_HI = 2,       /* mad.hi.u32: high half of a 32x32 product plus an addend */
-    PCPD_PIPE_IMAD_WIDE = 3,     /* mad.wide.u32: the whole 64-bit product plus a 64-bit addend */
-    PCPD_PIPE_IADD = 4,          /* two dependent add.u32 (a three-input add) */
-    PCPD_PIPE_MIX_LO_LOP3 = 5,   /* mad.lo and lop3 chains side by side (both counted) */
-    PCPD_PIPE_MIX_WIDE_LOP3 = 6, /* mad.wide and lop3 chains side by side (both counted) */
-    PCPD_PIPE_PHILOX_SPLIT = 7,  /* Philox4x32-10 blocks, products as high and low multiplies
-                                    (result in blocks, 3 independent blocks per iteration) */
-    PCPD_PIPE_PHILOX_WIDE = 8,   /* the same with one widening multiply per product */
-    PCPD_PIPE_COUNT = 9
+    PCPD_PIPE_LOP3 = 0,          /* lop3.b32 (three-input XOR), three register sources */
+    PCPD_PIPE_LOP3_2R = 1,       /* lop3.b32 with two register sources and an immediate */
+    PCPD_PIPE_IMAD_LO = 2,       /* mad.lo.u32: low half of a 32x32 product plus an addend
+                                    (two register sources) */
+    PCPD_PIPE_IMAD_LO_1R = 3,    /* mad.lo.u32 with one register source (constant factor and
+                                    addend) */
+    PCPD_PIPE_IMAD_HI = 4,       /* mul.hi.u32 by a constant: the high half of a product */
+    PCPD_PIPE_IMAD_WIDE = 5,     /* mul.wide.u32 by a constant, the form every Philox multiply
+                                    takes, its two halves XORed into the next factor (result in
+                                    products; the XORs run on the logic pipe beside them) */
+    PCPD_PIPE_IADD = 6,          /* two dependent add.u32 (a three-input add) */
+    PCPD_PIPE_MIX_LO_LOP3 = 7,   /* IMAD_LO and LOP3 chains side by side (both counted) */
+    PCPD_PIPE_MIX_LIGHT = 8,     /* IMAD_LO_1R and LOP3_2R chains side by side (both counted) */
+    PCPD_PIPE_MIX_WIDE_LOP3 = 9, /* IMAD_WIDE chains beside LOP3_2R chains (products and all
+                                    logic operations counted) */
+    PCPD_PIPE_PHILOX = 10,       /* Philox4x32-10 blocks on counters that all change every
+                                    iteration (result in blocks; 3 independent blocks per
+                                    iteration and thread) */
+    PCPD_PIPE_COUNT = 11
 };
 
 /* Run operation `op` for `iters` loop iterations on one CTA of `threads` threads (a multiple

@@ -12,6 +12,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <utility>
 #include <vector>
 
 #include "../../include/pcpd_pipes.h"
@@ -31,14 +32,25 @@ __device__ __forceinline__ uint32_t mad_lo(uint32_t a, uint32_t b, uint32_t c) {
   asm volatile("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
   return d;
 }
-__device__ __forceinline__ uint32_t mad_hi(uint32_t a, uint32_t b, uint32_t c) {
+// one source register each: the rest are immediates (no register read)
+__device__ __forceinline__ uint32_t lop3_xor_imm(uint32_t a, uint32_t b) {
   uint32_t d;
-  asm volatile("mad.hi.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  asm volatile("lop3.b32 %0, %1, %2, 0x5bd1e995, 0x96;" : "=r"(d) : "r"(a), "r"(b));
   return d;
 }
-__device__ __forceinline__ uint64_t mad_wide(uint32_t a, uint32_t b, uint64_t c) {
+__device__ __forceinline__ uint32_t mad_lo_imm(uint32_t a) {
+  uint32_t d;
+  asm volatile("mad.lo.u32 %0, %1, 0xD2511F53, 0x9E3779B9;" : "=r"(d) : "r"(a));
+  return d;
+}
+__device__ __forceinline__ uint32_t mul_hi_imm(uint32_t a) {
+  uint32_t d;
+  asm volatile("mul.hi.u32 %0, %1, 0xD2511F53;" : "=r"(d) : "r"(a));
+  return d;
+}
+__device__ __forceinline__ uint64_t mul_wide_imm(uint32_t a) {
   uint64_t d;
-  asm volatile("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+  asm volatile("mul.wide.u32 %0, %1, 0xD2511F53;" : "=l"(d) : "r"(a));
   return d;
 }
 __device__ __forceinline__ uint32_t add3(uint32_t a, uint32_t b, uint32_t c) {
@@ -49,28 +61,16 @@ __device__ __forceinline__ uint32_t add3(uint32_t a, uint32_t b, uint32_t c) {
 }
 
 // Philox4x32-10 (Salmon et al., SC'11): multipliers and Weyl increments of the published
-// definition.  SPLIT: each 64-bit product as a high and a low 32-bit multiply; else one
-// widening multiply.
+// definition.
 constexpr uint32_t kM0 = 0xD2511F53u, kM1 = 0xCD9E8D57u, kW0 = 0x9E3779B9u, kW1 = 0xBB67AE85u;
 
-template <bool SPLIT>
 __device__ __forceinline__ void philox(uint32_t &x0, uint32_t &x1, uint32_t &x2, uint32_t &x3, uint32_t k0,
                                        uint32_t k1) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    uint32_t h0, l0, h1, l1;
-    if (SPLIT) {
-      h0 = __umulhi(x0, kM0);
-      l0 = x0 * kM0;
-      h1 = __umulhi(x2, kM1);
-      l1 = x2 * kM1;
-    } else {
-      const uint64_t p0 = (uint64_t)x0 * kM0, p1 = (uint64_t)x2 * kM1;
-      h0 = (uint32_t)(p0 >> 32);
-      l0 = (uint32_t)p0;
-      h1 = (uint32_t)(p1 >> 32);
-      l1 = (uint32_t)p1;
-    }
+    const uint64_t p0 = (uint64_t)x0 * kM0, p1 = (uint64_t)x2 * kM1;
+    const uint32_t h0 = (uint32_t)(p0 >> 32), l0 = (uint32_t)p0;
+    const uint32_t h1 = (uint32_t)(p1 >> 32), l1 = (uint32_t)p1;
     x0 = h1 ^ x1 ^ k0;
     x1 = l1;
     x2 = h0 ^ x3 ^ k1;
@@ -94,16 +94,18 @@ __global__ void k_pipe(uint32_t iters, uint32_t seed, unsigned long long *cycles
   const uint32_t M = 0xD2511F53u ^ (seed & 0x10u);
   __syncthreads();
   const long long t0 = clock64();
-  if constexpr (OP == PCPD_PIPE_PHILOX_SPLIT || OP == PCPD_PIPE_PHILOX_WIDE) {
-    // three independent blocks per iteration (the sweep draws up to three per window)
+  if constexpr (OP == PCPD_PIPE_PHILOX) {
+    // three independent blocks per iteration (the sweep draws up to three per window); every
+    // counter word changes with the iteration, so no round can be hoisted out of the loop
     uint32_t acc = 0;
     for (uint32_t it = 0; it < iters; ++it) {
-      uint32_t a0 = threadIdx.x, a1 = it, a2 = blockIdx.x, a3 = 0u;
-      uint32_t b0 = threadIdx.x, b1 = it, b2 = blockIdx.x, b3 = 1u;
-      uint32_t c0 = threadIdx.x, c1 = it, c2 = blockIdx.x, c3 = 2u;
-      philox<OP == PCPD_PIPE_PHILOX_SPLIT>(a0, a1, a2, a3, seed, ~seed);
-      philox<OP == PCPD_PIPE_PHILOX_SPLIT>(b0, b1, b2, b3, seed, ~seed);
-      philox<OP == PCPD_PIPE_PHILOX_SPLIT>(c0, c1, c2, c3, seed, ~seed);
+      const uint32_t c = it * 0x9E3779B9u + threadIdx.x;
+      uint32_t a0 = c, a1 = it, a2 = c ^ blockIdx.x, a3 = it + 0u;
+      uint32_t b0 = c, b1 = it, b2 = c ^ blockIdx.x, b3 = it + 1u;
+      uint32_t c0 = c, c1 = it, c2 = c ^ blockIdx.x, c3 = it + 2u;
+      philox(a0, a1, a2, a3, seed, ~seed);
+      philox(b0, b1, b2, b3, seed, ~seed);
+      philox(c0, c1, c2, c3, seed, ~seed);
       acc ^= a0 ^ a1 ^ a2 ^ a3 ^ b0 ^ b1 ^ b2 ^ b3 ^ c0 ^ c1 ^ c2 ^ c3;
     }
     x[0] ^= acc;
@@ -114,15 +116,24 @@ __global__ void k_pipe(uint32_t iters, uint32_t seed, unsigned long long *cycles
         if constexpr (OP == PCPD_PIPE_LOP3) {
 #pragma unroll
           for (int j = 0; j < kChains; ++j) x[j] = lop3_xor(x[j], x[(j + 1) % kChains], x[(j + 2) % kChains]);
+        } else if constexpr (OP == PCPD_PIPE_LOP3_2R) {
+#pragma unroll
+          for (int j = 0; j < kChains; ++j) x[j] = lop3_xor_imm(x[j], x[(j + 1) % kChains]);
         } else if constexpr (OP == PCPD_PIPE_IMAD_LO) {
 #pragma unroll
           for (int j = 0; j < kChains; ++j) x[j] = mad_lo(x[j], M, x[(j + 1) % kChains]);
+        } else if constexpr (OP == PCPD_PIPE_IMAD_LO_1R) {
+#pragma unroll
+          for (int j = 0; j < kChains; ++j) x[j] = mad_lo_imm(x[j]);
         } else if constexpr (OP == PCPD_PIPE_IMAD_HI) {
 #pragma unroll
-          for (int j = 0; j < kChains; ++j) x[j] = mad_hi(x[j], M, x[(j + 1) % kChains]);
-        } else if constexpr (OP == PCPD_PIPE_IMAD_WIDE) {
+          for (int j = 0; j < kChains; ++j) x[j] = mul_hi_imm(x[j]);
+        } else if constexpr (OP == PCPD_PIPE_IMAD_WIDE) {   // each product's halves feed the next
 #pragma unroll
-          for (int j = 0; j < kChains; ++j) w[j] = mad_wide((uint32_t)w[j], M, w[(j + 1) % kChains]);
+          for (int j = 0; j < kChains; ++j) {
+            w[j] = mul_wide_imm(x[j]);
+            x[j] = lop3_xor_imm((uint32_t)w[j], (uint32_t)(w[j] >> 32));
+          }
         } else if constexpr (OP == PCPD_PIPE_IADD) {
 #pragma unroll
           for (int j = 0; j < kChains; ++j) x[j] = add3(x[j], x[(j + 1) % kChains], x[(j + 2) % kChains]);
@@ -132,11 +143,18 @@ __global__ void k_pipe(uint32_t iters, uint32_t seed, unsigned long long *cycles
             x[j] = mad_lo(x[j], M, x[(j + 1) % kChains]);
             y[j] = lop3_xor(y[j], y[(j + 1) % kChains], y[(j + 2) % kChains]);
           }
-        } else if constexpr (OP == PCPD_PIPE_MIX_WIDE_LOP3) {
+        } else if constexpr (OP == PCPD_PIPE_MIX_LIGHT) {   // the same with one or two register sources
 #pragma unroll
           for (int j = 0; j < kChains; ++j) {
-            w[j] = mad_wide((uint32_t)w[j], M, w[(j + 1) % kChains]);
-            y[j] = lop3_xor(y[j], y[(j + 1) % kChains], y[(j + 2) % kChains]);
+            x[j] = mad_lo_imm(x[j]);
+            y[j] = lop3_xor_imm(y[j], y[(j + 1) % kChains]);
+          }
+        } else if constexpr (OP == PCPD_PIPE_MIX_WIDE_LOP3) {   // widening products beside logic chains
+#pragma unroll
+          for (int j = 0; j < kChains; ++j) {
+            w[j] = mul_wide_imm(x[j]);
+            x[j] = lop3_xor_imm((uint32_t)w[j], (uint32_t)(w[j] >> 32));
+            y[j] = lop3_xor_imm(y[j], y[(j + 1) % kChains]);
           }
         }
       }
@@ -153,28 +171,22 @@ __global__ void k_pipe(uint32_t iters, uint32_t seed, unsigned long long *cycles
 
 using PipeKernel = void (*)(uint32_t, uint32_t, unsigned long long *, uint32_t *);
 
-PipeKernel kernel_of(int op) {
-  switch (op) {
-    case PCPD_PIPE_LOP3: return k_pipe<PCPD_PIPE_LOP3>;
-    case PCPD_PIPE_IMAD_LO: return k_pipe<PCPD_PIPE_IMAD_LO>;
-    case PCPD_PIPE_IMAD_HI: return k_pipe<PCPD_PIPE_IMAD_HI>;
-    case PCPD_PIPE_IMAD_WIDE: return k_pipe<PCPD_PIPE_IMAD_WIDE>;
-    case PCPD_PIPE_IADD: return k_pipe<PCPD_PIPE_IADD>;
-    case PCPD_PIPE_MIX_LO_LOP3: return k_pipe<PCPD_PIPE_MIX_LO_LOP3>;
-    case PCPD_PIPE_MIX_WIDE_LOP3: return k_pipe<PCPD_PIPE_MIX_WIDE_LOP3>;
-    case PCPD_PIPE_PHILOX_SPLIT: return k_pipe<PCPD_PIPE_PHILOX_SPLIT>;
-    case PCPD_PIPE_PHILOX_WIDE: return k_pipe<PCPD_PIPE_PHILOX_WIDE>;
-    default: return nullptr;
-  }
+template <int... OPS>
+PipeKernel pick(int op, std::integer_sequence<int, OPS...>) {
+  PipeKernel k = nullptr;
+  ((op == OPS ? (k = k_pipe<OPS>, 0) : 0), ...);
+  return k;
 }
+
+PipeKernel kernel_of(int op) { return pick(op, std::make_integer_sequence<int, PCPD_PIPE_COUNT>{}); }
 
 // Operations one thread performs per loop iteration, in the unit of the result.
 double ops_per_iter(int op) {
   switch (op) {
-    case PCPD_PIPE_PHILOX_SPLIT:
-    case PCPD_PIPE_PHILOX_WIDE: return 3.0;   // Philox blocks
+    case PCPD_PIPE_PHILOX: return 3.0;   // Philox blocks
     case PCPD_PIPE_MIX_LO_LOP3:
-    case PCPD_PIPE_MIX_WIDE_LOP3: return 2.0 * kChains * kUnroll;   // both kinds counted
+    case PCPD_PIPE_MIX_LIGHT: return 2.0 * kChains * kUnroll;   // both kinds counted
+    case PCPD_PIPE_MIX_WIDE_LOP3: return 3.0 * kChains * kUnroll;   // products and both logic ops
     default: return (double)kChains * kUnroll;
   }
 }

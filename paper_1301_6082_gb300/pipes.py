@@ -13,10 +13,10 @@ import os
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpcpd_pipes.so")
 
-OPS = ["lop3", "imad_lo", "imad_hi", "imad_wide", "iadd3", "mix_imad_lo_lop3", "mix_imad_wide_lop3",
-       "philox_split", "philox_wide"]
+OPS = ["lop3", "lop3_2r", "imad_lo", "imad_lo_1r", "imad_hi", "imad_wide", "iadd3", "mix_imad_lo_lop3",
+       "mix_light", "mix_imad_wide_lop3", "philox"]
 # loop iterations per op: each launch runs a few milliseconds
-_ITERS = {"philox_split": 2000, "philox_wide": 2000}
+_ITERS = {"philox": 2000}
 
 _lib = None
 
@@ -52,8 +52,7 @@ def all_rates(threads: int = 1024) -> dict:
     for op in OPS:
         v, ms = rate(op, threads=threads)
         out[op] = round(v, 2)
-    for op in ("philox_split", "philox_wide"):
-        out[op + "_products"] = round(20.0 * out[op], 2)
+    out["philox_products"] = round(20.0 * out["philox"], 2)
     return out
 
 
