@@ -15,7 +15,7 @@
  * Canonical lattice layout (every host or device buffer that holds a lattice):
  *     uint32_t words[G][L], G = samples/32; bit j of words[g][i] = occupation of sample
  *     32*g + j at site i.
- * Random numbers: Philox4x32-10 keyed by the seed and counted by (window, sub-step, group,
+ * Random numbers: Philox4x32-10 keyed by the seed and counted by (sub-step, window, group,
  * tag|block), so results do not depend on how the work is split or batched.
  *
  * Conventions for every function returning int: 0 (PCPD_OK) on success, else one of the
@@ -135,7 +135,7 @@ int pcpd_pair_density(const pcpd_t *h, double *rho_pair_out, size_t n_times);
 int pcpd_sample_counts(const pcpd_t *h, size_t r, uint32_t *out);
 
 /* Checkpoint and resume.  The paper is silent on both; resuming is exact here because every
- * random word is addressed by (seed, window, sub-step, group, block), so the state of a run is
+ * random word is addressed by (seed, sub-step, window, group, block), so the state of a run is
  * just its lattice and its sub-step counter.
  * Copy the current lattice to host memory in the canonical layout (G*L words).  Waits. */
 int pcpd_get_lattice(const pcpd_t *h, uint32_t *host_out);

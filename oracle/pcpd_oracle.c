@@ -12,7 +12,7 @@
  *   - with one rate draw u per sample and window, compared with integer thresholds
  *     floor(rate * 2^32), the exact generalisation of the dyadic masks of Sec. 4.2-4.3;
  *   - random bits from Philox4x32-10 (Salmon et al., SC'11), keyed by seed and counted by
- *     (window, sub-step, group, tag|block);
+ *     (sub-step, window, group, tag|block);
  *   - and, separately, Alg. 1 itself (random-sequential updates) as a statistical reference.
  *
  * Every sample is simulated one at a time on a byte per site.  All 32 bit planes of u are
@@ -246,7 +246,7 @@ static void *orc_worker(void *arg)
                 /* 33 words: O and planes P31..P0 (blocks 0..8) */
                 uint32_t words[36];
                 for (uint32_t b = 0; b < 9; ++b)
-                    orc_block(jb->seed, k, (uint32_t)n, gk, (ORC_TAG_DYN << 28) | b, words + 4 * b);
+                    orc_block(jb->seed, (uint32_t)n, k, gk, (ORC_TAG_DYN << 28) | b, words + 4 * b);
                 const uint32_t O = words[0];
                 /* plane P_m is words[32 - m] for m = 31..0 */
                 uint32_t site[8];

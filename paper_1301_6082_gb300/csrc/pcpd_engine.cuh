@@ -219,9 +219,11 @@ __device__ __forceinline__ void run_item(const InstDesc &D, uint32_t *smem, uint
       Cmp cD = cmp_init(D.T.td, D.T.td_full), cA = cmp_init(D.T.tda, D.T.tda_full);
       uint32_t O;
       {
-        uint32_t x0 = k, x1 = n, x2 = g, x3 = kTagDyn << 28;
-        uint32_t y0 = k, y1 = n, y2 = g, y3 = (kTagDyn << 28) | 1u;
-        uint32_t z0 = k, z1 = n, z2 = g, z3 = (kTagDyn << 28) | 2u;
+        // the window index enters through a counter word that round 1 XORs rather than
+        // multiplies: the products that depend on (n, g) alone stay out of the window loop
+        uint32_t x0 = n, x1 = k, x2 = g, x3 = kTagDyn << 28;
+        uint32_t y0 = n, y1 = k, y2 = g, y3 = (kTagDyn << 28) | 1u;
+        uint32_t z0 = n, z1 = k, z2 = g, z3 = (kTagDyn << 28) | 2u;
         philox4x32_10_rk(x0, x1, x2, x3, rk);
         philox4x32_10_rk(y0, y1, y2, y3, rk);
         philox4x32_10_rk(z0, z1, z2, z3, rk);

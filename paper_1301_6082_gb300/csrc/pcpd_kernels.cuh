@@ -8,7 +8,7 @@
 // draw u with integer thresholds floor(rate*2^32), bit-sliced over 32 random "planes" and
 // evaluated most-significant plane first with an early exit -- the exact generalisation of
 // the dyadic AND/OR masks of Sec. 4.2-4.3.  Random words come from Philox4x32-10 (Salmon et
-// al., SC'11) keyed by the seed and counted by (window, sub-step, group, tag|block).  The
+// al., SC'11) keyed by the seed and counted by (sub-step, window, group, tag|block).  The
 // triplet and quadruplet processes (TCPD, QCPD) use the same draws on windows of 4 and 5
 // sites (window_update_n).
 #pragma once
@@ -160,9 +160,9 @@ __device__ __forceinline__ bool cmp_open2(const Cmp &c, uint32_t lo, int m_lo) {
   return c.eq != 0u && (uint32_t)m_lo > lo;
 }
 
-// Rate masks of one (window k, sub-step n, group g): D = lanes with u < T_D (diffuse),
+// Rate masks of one (sub-step n, window k, group g): D = lanes with u < T_D (diffuse),
 // A = lanes with T_D <= u < T_DA (annihilate an occupied bond), O = orientation bits.
-// Block b of the counter (k, n, g, b) holds (O, P31, P30, P29) for b = 0 and
+// Block b of the counter (n, k, g, b) holds (O, P31, P30, P29) for b = 0 and
 // (P_{32-4b} .. P_{29-4b}) for b >= 1; block 8 holds P0 in its first word.
 struct Masks {
   uint32_t D, A, O;
@@ -170,20 +170,21 @@ struct Masks {
 
 // One window (a, b, c) for 32 samples of the PCPD (Alg. 1's tree on the bond the orientation picks,
 // written as bit logic like Alg. 2).  Lane with o=0: bond (a,b), fission target c; o=1: bond
-// (b,c), target a.  D: swap the bond; A: clear an occupied bond; otherwise (F) fill the
-// target next to an occupied bond.
-__device__ __forceinline__ void window_update(uint32_t &a, uint32_t &b, uint32_t &c,
-                                              const Masks &m) {
-  const uint32_t q = (m.O & c) | (~m.O & a);   // partner of b
-  const uint32_t t = (m.O & a) | (~m.O & c);   // fission target
-  const uint32_t pair = b & q;                 // occupied bond
-  const uint32_t xb = b ^ (m.A & pair);        // b after an annihilation
-  const uint32_t xq = q ^ (m.A & pair);        // partner after an annihilation
-  const uint32_t nb = (m.D & q) | (~m.D & xb); // a diffusion swaps b and its partner
-  const uint32_t nq = (m.D & b) | (~m.D & xq);
-  const uint32_t nt = t | (pair & ~(m.D | m.A)); // fission fills the target
-  a = (m.O & nt) | (~m.O & nq);
-  c = (m.O & nq) | (~m.O & nt);
+// (b,c), target a.  ltD = lanes with u < T_D: swap the bond; ltA = lanes with u < T_DA, which
+// contains ltD: those that do not swap clear an occupied bond; the rest (u >= T_DA) fill the
+// target next to an occupied bond.  A swapping lane ignores the clear, so the clear can be
+// written with ltA rather than ltA & ~ltD (one operation fewer, same bits).
+__device__ __forceinline__ void window_update(uint32_t &a, uint32_t &b, uint32_t &c, uint32_t O,
+                                              uint32_t ltD, uint32_t ltA) {
+  const uint32_t q = (O & c) | (~O & a);         // partner of b
+  const uint32_t t = (O & a) | (~O & c);         // fission target
+  const uint32_t xb = b & ~(ltA & q);            // b after an annihilation
+  const uint32_t xq = q & ~(ltA & b);            // partner after an annihilation
+  const uint32_t nb = (ltD & q) | (~ltD & xb);   // a diffusion swaps b and its partner
+  const uint32_t nq = (ltD & b) | (~ltD & xq);
+  const uint32_t nt = t | (b & q & ~ltA);        // fission fills the target
+  a = (O & nt) | (~O & nq);
+  c = (O & nq) | (~O & nt);
   b = nb;
 }
 
@@ -347,7 +348,7 @@ __device__ __forceinline__ void finish_from3(uint32_t k, uint32_t n, uint32_t g,
   for (int b = 3; b <= 8; ++b) {
     const int m_prev = 33 - 4 * b;
     if (!cmp_open2(cD, T.lo_d, m_prev) && !cmp_open2(cA, T.lo_da, m_prev)) break;
-    uint32_t x0 = k, x1 = n, x2 = g, x3 = (kTagDyn << 28) | (uint32_t)b;
+    uint32_t x0 = n, x1 = k, x2 = g, x3 = (kTagDyn << 28) | (uint32_t)b;
     philox4x32_10_rk(x0, x1, x2, x3, rk);
     if (b < 8) {
       const uint32_t w[4] = {x0, x1, x2, x3};
@@ -368,17 +369,18 @@ __device__ __forceinline__ void apply_window(uint32_t *sm, const uint32_t (&idx)
   for (int j = 0; j < W; ++j)
     if (!PCPD_IN_BOUNDS(idx[j], lim, kDbgWindow)) return;
   (void)lim;
-  Masks m;
-  m.D = ltD;
-  m.A = ltA & ~ltD;   // T_D <= u < T_DA
-  m.O = O;
   uint32_t s[W];
 #pragma unroll
   for (int j = 0; j < W; ++j) s[j] = sm[idx[j]];
-  if constexpr (W == 3)
-    window_update(s[0], s[1], s[2], m);
-  else
+  if constexpr (W == 3) {
+    window_update(s[0], s[1], s[2], O, ltD, ltA);
+  } else {
+    Masks m;
+    m.D = ltD;
+    m.A = ltA & ~ltD;   // T_D <= u < T_DA
+    m.O = O;
     window_update_n<W>(s, m);
+  }
 #pragma unroll
   for (int j = 0; j < W; ++j) sm[idx[j]] = s[j];
 }
