@@ -56,10 +56,16 @@ def test_noalloc_matches_allocating_path_twice(P, L, S, p, d, n1, n2):
 
 
 def test_noalloc_rejects_oversized_work(P):
+    import ctypes as C
     import torch
     a = torch.zeros(8, dtype=torch.int32, device="cuda")
     b = torch.zeros(8, dtype=torch.int32, device="cuda")
-    # 2^22 samples on 65536 sites: 131072 columns x 2 segments, beyond the fixed scratch
-    with pytest.raises(P.PcpdError) as e:
+    # 2^22 samples on 65536 sites: 131072 columns x 2 segments, beyond the fixed scratch.  The
+    # C entry point refuses before touching the (deliberately small) buffers; the binding
+    # would refuse them earlier for their size, so the entry point is called directly.
+    rc = P.load().pcpd_sweep_noalloc(C.c_void_p(a.data_ptr()), C.c_void_p(b.data_ptr()), 65536, 1 << 22,
+                                     0.1, 0.5, 1, 0, 10, None)
+    assert rc == P.PCPD_EINVAL and "scratch" in P.load().pcpd_last_error().decode()
+    with pytest.raises(P.PcpdError) as e:   # and the binding refuses the small buffers themselves
         P.sweep_noalloc(a, b, 65536, 1 << 22, 0.1, 0.5, 1, 0, 10)
-    assert e.value.code == P.PCPD_EINVAL and "scratch" in str(e.value)
+    assert e.value.code == P.PCPD_EINVAL and "lat_in" in str(e.value)
