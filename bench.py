@@ -41,11 +41,13 @@ TRAFFIC_PER_LAUNCH = 38.21e6 + 1767.53e6
 UNIT = "attempts/s"
 
 
-# Integer pipe rates per SM and clock on this GPU: 32-bit logic / compare / shift (LOP3 and
-# kin) on the 64-lane ALU pipe; 32x32->64-bit multiplies (Philox's mul.wide) at 32 per clock
-# on the FMA pipe.  Both agree with the documented per-SM integer throughputs and with a
-# microbenchmark (independent chains: LOP3 and IMAD 60, IMAD.WIDE 24-32, IADD 119, FFMA 115
-# per SM per clock at 2.07 GHz; Philox4x32-10 alone 5.05e11 blocks/s = 32 wide multiplies).
+# Integer pipe rates per SM and clock on this GPU (the unit counts: 4 sub-partitions, each
+# with a 16-lane ALU pipe and a 16-lane FMA-heavy pipe): 32-bit logic / compare / shift (LOP3
+# and kin) take the ALU pipe 2 cycles per warp instruction, 64 lanes per SM and clock; a
+# 32x32->64-bit product (Philox's widening multiply, one instruction per product) takes the
+# FMA-heavy pipe 4 cycles, 32 products per SM and clock.  The pipe-rate kernels of
+# libpcpd_pipes.so measure both (64.0 and 32.0; a pure Philox4x32-10 stream 1.60 blocks =
+# 32.0 products per SM and clock), and the bench re-measures the Philox rate on every run.
 LOGIC_LANES = 64
 WIDE_MUL_LANES = 32
 
@@ -476,9 +478,9 @@ def compact(d, keys):
 def compact_roofline(r):
     """The roofline entries the headline line carries; the notes go to the detail line."""
     keep = ("bound", "achieved", "peak", "unit", "frac", "traffic", "binding_pipe", "frac_logic_pipe",
-            "frac_of_issue_slots", "peak_source")
+            "frac_of_issue_slots", "peak_measured")
     out = {k: r[k] for k in keep if k in r}
-    for k in ("achieved", "peak", "frac", "frac_logic_pipe", "frac_of_issue_slots"):
+    for k in ("achieved", "peak", "frac", "frac_logic_pipe", "frac_of_issue_slots", "peak_measured"):
         if isinstance(out.get(k), float):
             out[k] = round(out[k], 4)
     return out
@@ -608,6 +610,14 @@ def main():
     mul_item = sum(i * o[3] for i, o in zip(items, ops_item)) / sum(items)
     logic_item = sum(i * o[4] for i, o in zip(items, ops_item)) / sum(items)
     plan0 = sims[0].plan()
+    pipe_rates = None
+    try:   # the measured peak beside the derived one: a pure Philox stream on this GPU
+        from paper_1301_6082_gb300 import pipes as PR
+        B.build_pipes()
+        pipe_rates = {op: round(PR.rate(op)[0], 2) for op in ("philox", "imad_wide", "lop3")}
+        pipe_rates["philox_products"] = round(20.0 * pipe_rates["philox"], 2)
+    except Exception as exc:   # reported, not fatal: the derived peak stands
+        pipe_rates = {"error": str(exc)[:200]}
     kname = "pcpd_jit_sweep (engine compiled for the run's thresholds)" if plan0.get("jit") else "k_sweep_persistent"
     issue_peak = sm_count * 4 * 32 * sm_max_mhz * 1e6 / 1e12   # T lane-ops/s, all pipes together
     roofline = {"bound": "alu", **pipe_roofline(items_s, mul_item, logic_item, sm_count, sm_max_mhz),
@@ -619,7 +629,10 @@ def main():
                                  "(the three runs on their own streams) / the region's CUDA-event duration",
                 "wide_multiplies_per_item": round(mul_item, 2), "logic_ops_per_item": round(logic_item, 2),
                 "expected_philox_blocks_per_item": [round(o[1], 3) for o in ops_item],
-                "frac_of_issue_slots": (alg_ops / (ms / 1e3)) / 1e12 / issue_peak}
+                "frac_of_issue_slots": (alg_ops / (ms / 1e3)) / 1e12 / issue_peak,
+                "measured_lanes_per_sm_clock": pipe_rates,
+                "peak_measured": (pipe_rates.get("philox_products", 0) * sm_count * sm_max_mhz * 1e6 / 1e12
+                                  if "philox_products" in pipe_rates else None)}
 
     # end to end through the public API with host buffers (pinned), host<->device in the region:
     # each run on its own stream, so one run's copies overlap another run's sweep

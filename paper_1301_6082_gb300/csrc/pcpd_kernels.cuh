@@ -369,20 +369,24 @@ __device__ __forceinline__ void apply_window(uint32_t *sm, const uint32_t (&idx)
   for (int j = 0; j < W; ++j)
     if (!PCPD_IN_BOUNDS(idx[j], lim, kDbgWindow)) return;
   (void)lim;
-  uint32_t s[W];
-#pragma unroll
-  for (int j = 0; j < W; ++j) s[j] = sm[idx[j]];
   if constexpr (W == 3) {
-    window_update(s[0], s[1], s[2], O, ltD, ltA);
+    uint32_t a = sm[idx[0]], b = sm[idx[1]], c = sm[idx[2]];
+    window_update(a, b, c, O, ltD, ltA);
+    sm[idx[0]] = a;
+    sm[idx[1]] = b;
+    sm[idx[2]] = c;
   } else {
+    uint32_t s[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) s[j] = sm[idx[j]];
     Masks m;
     m.D = ltD;
     m.A = ltA & ~ltD;   // T_D <= u < T_DA
     m.O = O;
     window_update_n<W>(s, m);
-  }
 #pragma unroll
-  for (int j = 0; j < W; ++j) sm[idx[j]] = s[j];
+    for (int j = 0; j < W; ++j) sm[idx[j]] = s[j];
+  }
 }
 
 // Initial lattice: mode 0 full, 1 empty, 2 i.i.d. Bernoulli(1/2) bits (Philox tag INIT,
