@@ -37,7 +37,16 @@ METRIC = "attempted site updates/s"
 # dram__bytes_read.sum + dram__bytes_write.sum of one bench-size launch of the specialised
 # sweep (one run advanced 2000 MCS; two 256-thread CTAs per SM, tiles 21848 + 2 x 132 sites,
 # tau = 64), 1-pass ncu capture (profiles/pcpd_jit_sweep_L65536_S4096.md)
-TRAFFIC_PER_LAUNCH = 38.21e6 + 1767.53e6
+TRAFFIC_PER_LAUNCH = 38.33e6 + 1795.51e6
+# Executed work per (window, group) item of that sweep, from the same capture (d = 1/2):
+# widening products = 2 per window + 14 per Philox block x 3.03 blocks (4 FMA-heavy cycles per
+# warp instruction), 22.8 other multiply-adds (2 cycles), 30.32 active lanes per warp
+# instruction, 1.2% of windows recomputed in tile halos.  Used to predict the FMA-heavy pipe's
+# activity from the timed rate, for comparison with ncu's.
+EXEC_WIDE_PER_ITEM = 2.0 + 14.0 * 3.03
+EXEC_IMAD_PER_ITEM = 22.8
+EXEC_ACTIVE_LANES = 30.32
+EXEC_HALO = 1.012
 UNIT = "attempts/s"
 
 
@@ -478,9 +487,10 @@ def compact(d, keys):
 def compact_roofline(r):
     """The roofline entries the headline line carries; the notes go to the detail line."""
     keep = ("bound", "achieved", "peak", "unit", "frac", "traffic", "binding_pipe", "frac_logic_pipe",
-            "frac_of_issue_slots", "peak_measured")
+            "frac_of_issue_slots", "peak_measured", "fmaheavy_active_pred")
     out = {k: r[k] for k in keep if k in r}
-    for k in ("achieved", "peak", "frac", "frac_logic_pipe", "frac_of_issue_slots", "peak_measured"):
+    for k in ("achieved", "peak", "frac", "frac_logic_pipe", "frac_of_issue_slots", "peak_measured",
+              "fmaheavy_active_pred"):
         if isinstance(out.get(k), float):
             out[k] = round(out[k], 4)
     return out
@@ -631,6 +641,8 @@ def main():
                 "expected_philox_blocks_per_item": [round(o[1], 3) for o in ops_item],
                 "frac_of_issue_slots": (alg_ops / (ms / 1e3)) / 1e12 / issue_peak,
                 "measured_lanes_per_sm_clock": pipe_rates,
+                "fmaheavy_active_pred": items_s * (EXEC_WIDE_PER_ITEM * 4 + EXEC_IMAD_PER_ITEM * 2) / EXEC_ACTIVE_LANES
+                * EXEC_HALO / (4 * sm_count * sm_max_mhz * 1e6),
                 "peak_measured": (pipe_rates.get("philox_products", 0) * sm_count * sm_max_mhz * 1e6 / 1e12
                                   if "philox_products" in pipe_rates else None)}
 

@@ -65,8 +65,9 @@ typedef struct pcpd_params {
     int per_sample;      /* non-zero: also keep per-sample counts at every record */
     /* plan override, 0 = automatic.  No plan changes a result bit.  Automatic: columns that
        fit one CTA's shared memory are whole-column tiles; longer columns are cut into tiles
-       sized for two 256-thread CTAs per SM with tau = 64 (handles in batches and servers:
-       one 512-thread CTA per SM with the largest tile, tau = 128). */
+       sized for two 256-thread CTAs per SM with tau = 64 (batch and server members: every
+       tile, whole-column or not, sized for two CTAs of at most 256 threads per SM, so that a
+       launch of any mix of members runs two CTAs per SM). */
     uint32_t plan_threads;   /* threads per CTA (multiple of 32 in [64, 512]) */
     uint32_t plan_seg_sites; /* core sites per tile for lattices that do not fit one CTA */
     uint32_t plan_tau;       /* sub-steps per tile residency (temporal block) */

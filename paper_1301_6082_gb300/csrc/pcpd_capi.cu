@@ -370,12 +370,20 @@ int jit_function(uint32_t td, uint32_t tda, uint32_t W, CUfunction *out) {
 
 // Tile plan.  Columns that fit in shared memory run as RING tiles (whole columns, gpi of them
 // per CTA when they are short, so that a CTA has enough windows per sub-step); longer columns
-// are cut into equal SEGMENT tiles with a halo of (W-1)*tau + W + 1 sites.  PAIRED: SEGMENT
-// tiles are sized so that two CTAs of 256 threads share an SM (one CTA's barriers and
-// deferred-window tail overlap the other's first pass), with tau = 64; otherwise one CTA of
-// kSweepThreads per SM holds the largest tile, tau = 128 (batched launches, which run every
-// instance with one CTA shape, and the allocation-free sweep).  No plan changes a result bit.
-int make_plan(pcpd_t *h, const pcpd_params *prm, bool paired = false) {
+// are cut into equal SEGMENT tiles with a halo of (W-1)*tau + W + 1 sites.  Modes:
+//  kPlanPaired (a lone instance): SEGMENT tiles sized so that two CTAs of 256 threads share an
+//    SM (one CTA's barriers and deferred-window tail overlap the other's first pass), tau =
+//    64, and columns cut into enough tiles for every SM;
+//  kPlanPairedBatch (batch and server members, which share one CTA shape per launch): every
+//    tile, RING or SEGMENT, fits half an SM and CTAs have at most 256 threads, so a launch of
+//    any mix of members runs two CTAs per SM;
+//  kPlanOne (the allocation-free sweep, and the fallback of the others): one CTA of
+//    kSweepThreads per SM holds the largest tile, tau = 128.
+// No plan changes a result bit.
+enum PlanMode { kPlanOne = 0, kPlanPaired = 1, kPlanPairedBatch = 2 };
+
+int make_plan(pcpd_t *h, const pcpd_params *prm, PlanMode mode = kPlanOne) {
+  const bool paired = mode != kPlanOne, batch = mode == kPlanPairedBatch;
   int optin = 0, dev = 0, sms = 0;
   int rc = smem_optin(&optin);
   if (rc) return rc;
@@ -398,8 +406,8 @@ int make_plan(pcpd_t *h, const pcpd_params *prm, bool paired = false) {
   if (h->tau == 0u) return fail(PCPD_EINVAL, "plan_tau must be positive");
   // Segment tiles below this many core sites cost more in halo windows than they give.
   constexpr uint32_t kMinCore = 4096u;
-  bool ring = seg_override == 0 && L <= avail_words;
-  if (paired && ring && h->G < (uint32_t)sms) {
+  bool ring = seg_override == 0 && L <= (batch ? pair_words : avail_words);
+  if (paired && !batch && ring && h->G < (uint32_t)sms) {
     // fewer whole columns than SMs would leave SMs idle: cut the columns into segments
     // instead, when two segments of a useful length fit
     const uint32_t tau = (prm && prm->plan_tau) ? prm->plan_tau : 64u;
@@ -414,14 +422,15 @@ int make_plan(pcpd_t *h, const pcpd_params *prm, bool paired = false) {
     // columns per tile: up to 4 (one phase group), while they fit, the CTA lacks windows and
     // there are still enough tiles to give every SM one
     uint32_t gpi = 1;
-    while (gpi < 4 && h->G % (2 * gpi) == 0 && (size_t)(2 * gpi) * L <= avail_words && gpi * h->K < 4096 &&
-           h->G / (2 * gpi) >= (uint32_t)sms)
+    while (gpi < 4 && h->G % (2 * gpi) == 0 && (size_t)(2 * gpi) * L <= (batch ? pair_words : avail_words) &&
+           gpi * h->K < 4096 && h->G / (2 * gpi) >= (uint32_t)sms)
       gpi *= 2;
     h->gpi = gpi;
     // a RING tile keeps its columns for a long stretch of sub-steps
     h->tau = (prm && prm->plan_tau) ? prm->plan_tau : (1u << 20);
     uint32_t want = (gpi * h->K + 31u) / 32u * 32u;
-    if (want > pcpdk::kSweepThreads) want = pcpdk::kSweepThreads;
+    const uint32_t cap = batch ? 256u : pcpdk::kSweepThreads;
+    if (want > cap) want = cap;
     if (want < 64u) want = 64u;
     h->threads = want;
     h->tile_words = (size_t)gpi * L;
@@ -438,11 +447,11 @@ int make_plan(pcpd_t *h, const pcpd_params *prm, bool paired = false) {
       const size_t budget = paired ? pair_words : avail_words;
       const size_t max_core = budget > 2u * h->halo ? budget - 2u * h->halo : 0;
       if (max_core < 1024) {
-        if (paired) return make_plan(h, prm, false);
+        if (paired) return make_plan(h, prm, kPlanOne);
         return fail(PCPD_EINVAL, "temporal block tau=%u too large for shared memory", h->tau);
       }
       uint32_t nseg = std::max<uint32_t>(2u, (uint32_t)((L + max_core - 1) / max_core));
-      if (paired) {
+      if (paired && !batch) {
         // enough tiles per epoch for the two CTAs of every SM, while tiles stay long
         while ((uint64_t)h->G * nseg < 2ull * (uint64_t)sms && (L + nseg) / (nseg + 1u) >= kMinCore) ++nseg;
       }
@@ -471,11 +480,11 @@ int make_plan(pcpd_t *h, const pcpd_params *prm, bool paired = false) {
   if (rc) return rc;
   int per_sm = 0;
   CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel(false, h->W), (int)h->threads, h->dyn_smem));
-  if (paired && !h->ring && per_sm < 2) return make_plan(h, prm, false);   // the pair does not fit
+  if (paired && (batch || !h->ring) && per_sm < 2) return make_plan(h, prm, kPlanOne);   // the pair does not fit
   if (per_sm < 1) return fail(PCPD_EINVAL, "tile plan does not fit one CTA per SM");
   h->grid = per_sm * sms;
   const uint64_t tiles = (uint64_t)(h->G / h->gpi) * h->n_seg;
-  if (paired && !h->ring && tiles >= (1ull << 24)) return make_plan(h, prm, false);   // longer tiles
+  if (paired && !h->ring && tiles >= (1ull << 24)) return make_plan(h, prm, kPlanOne);   // longer tiles
   if (tiles >= (1ull << 24))   // a work item carries the tile index in 24 bits
     return fail(PCPD_EINVAL, "%llu tiles per epoch (at most 2^24 - 1): fewer samples or longer tiles",
                 (unsigned long long)tiles);
@@ -749,7 +758,7 @@ int create_handle(const pcpd_params *prm, pcpd_t **out, bool batch_member) {
     pcpd_destroy(h);
     return code;
   };
-  rc = make_plan(h, prm, !batch_member);
+  rc = make_plan(h, prm, batch_member ? kPlanPairedBatch : kPlanPaired);
   if (rc) return bail(rc);
   if (prm->stream) {
     h->stream = (cudaStream_t)prm->stream;
@@ -1251,11 +1260,13 @@ int run_multi(cudaStream_t stream, uint32_t *d_ctl, unsigned long long **d_items
     const size_t c1 = std::min(n, c0 + (size_t)pcpdk::kMaxBatchInst);
     std::vector<pcpdk::InstDesc> desc(c1 - c0);
     size_t tile_words = 0;
+    uint32_t threads = 64;   // the launch takes the largest CTA any member's plan asks for
     for (size_t i = c0; i < c1; ++i) {
       pcpd_t *h = tg[i].h;
       fill_desc(h, desc[i - c0], h->n_now, tg[i].n_end, tg[i].rec_first, tg[i].rec_first + tg[i].rec_taken,
                 tg[i].slot0);
       tile_words = std::max(tile_words, h->tile_words);
+      threads = std::max(threads, h->threads);
     }
     std::vector<std::pair<double, unsigned long long>> ring_items;
     std::vector<unsigned long long> items;
@@ -1321,7 +1332,6 @@ int run_multi(cudaStream_t stream, uint32_t *d_ctl, unsigned long long **d_items
     B.err = d_ctl + 1;
     B.tile_words = (uint32_t)tile_words;
     B.spin_limit = kSpinLimit;
-    const uint32_t threads = pcpdk::kSweepThreads;
     const size_t dyn = 4 * (tile_words + pcpdk::sweep_queue_words(32));
     if (dyn + kStaticSmem > (size_t)optin) return fail(PCPD_EINVAL, "batch tile exceeds shared memory");
     {
@@ -2048,7 +2058,7 @@ extern "C" int pcpd_autotune(const pcpd_params *prm, uint32_t trial_substeps, pc
   rc = make_plan(&base, nullptr);
   if (rc) return rc;
   pcpd paired = base;   // the tile two CTAs per SM can hold
-  rc = make_plan(&paired, nullptr, true);
+  rc = make_plan(&paired, nullptr, kPlanPaired);
   if (rc) return rc;
   struct Cand {
     uint32_t threads, seg, tau;

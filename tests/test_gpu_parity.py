@@ -144,11 +144,11 @@ def test_segmented_plan_bit_exact_and_plan_invariant(P, oracle_mod, L, seg, tau,
     np.testing.assert_array_equal(a.lattice(), oracle_mod.pack(st))
 
 
-def test_default_plans_two_ctas_per_sm_alone_one_in_batches(P, oracle_mod):
+def test_default_plans_two_ctas_per_sm_alone_and_in_batches(P, oracle_mod):
     """A lone instance whose columns exceed one CTA's shared memory runs two 256-thread CTAs
-    per SM (tau = 64); the same instance in a batch runs one 512-thread CTA per SM with the
-    largest tile (tau = 128). Both give the oracle's bits, and so does the one-CTA plan forced
-    on a lone instance."""
+    per SM (tau = 64), and so does the same instance in a batch (every batch member's tile fits
+    half an SM). Both give the oracle's bits, and so does the one-CTA plan forced on a lone
+    instance (one 512-thread CTA per SM, the largest tile, tau = 128)."""
     import torch
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     L, S, p, d, seed, mcs = 65536, 64, 0.15, 0.5, 5, 3
