@@ -205,7 +205,18 @@ __device__ __forceinline__ void run_item(const InstDesc &D, uint32_t *smem, uint
     const uint32_t n_cand = RING ? n_cand_ring : G.n_cand;
 
     // ---- first pass: blocks 0-2 for every window; undecided windows are deferred ----
-    for (uint32_t i0 = warp * 32u; i0 < n_cand; i0 += blockDim.x) {
+    // SEGMENT tiles advance each thread's window index and first site incrementally (the index
+    // wraps from K-1 to 0 at most once per sub-step, adding the idle gap to the site) and test
+    // the site range with one unsigned compare; candidates past n_cand land beyond the range
+    const uint32_t stride = blockDim.x;
+    uint32_t seg_k = G.k_lo + warp * 32u + lane;
+    int seg_y = G.y_first + W * (int)(warp * 32u + lane);
+    if (!RING && seg_k >= K) {
+      seg_k -= K;
+      seg_y += (int)G.gap;
+    }
+    const uint32_t span = G.hi - G.lo - (uint32_t)(W - 1);   // first sites [lo, hi - W + 1)
+    for (uint32_t i0 = warp * 32u; i0 < n_cand; i0 += stride) {
       const uint32_t i = i0 + lane;
       uint32_t col = 0, ii = i;
       if (RING) {
@@ -213,7 +224,21 @@ __device__ __forceinline__ void run_item(const InstDesc &D, uint32_t *smem, uint
         ii = i - col * K;
       }
       uint32_t k = 0, idx[W] = {};
-      const bool valid = i < n_cand && candidate<RING, W>(G, ii, L, K, k, idx);
+      bool valid;
+      if (RING) {
+        valid = i < n_cand && candidate<RING, W>(G, ii, L, K, k, idx);
+      } else {
+        k = seg_k;
+        valid = (uint32_t)(seg_y - (int)G.lo) < span;
+#pragma unroll
+        for (int j2 = 0; j2 < W; ++j2) idx[j2] = (uint32_t)(seg_y + j2);
+        seg_k += stride;
+        seg_y += W * (int)stride;
+        if (seg_k >= K) {
+          seg_k -= K;
+          seg_y += (int)G.gap;
+        }
+      }
       uint32_t *sm = smem + col * L;
       const uint32_t g = D.g_base + g0 + col;   // the group's index in the Philox counter
       Cmp cD = cmp_init(D.T.td, D.T.td_full), cA = cmp_init(D.T.tda, D.T.tda_full);
