@@ -37,15 +37,15 @@ METRIC = "attempted site updates/s"
 # dram__bytes_read.sum + dram__bytes_write.sum of one bench-size launch of the specialised
 # sweep (one run advanced 2000 MCS; two 256-thread CTAs per SM, tiles 21848 + 2 x 132 sites,
 # tau = 64), 1-pass ncu capture (profiles/pcpd_jit_sweep_L65536_S4096.md)
-TRAFFIC_PER_LAUNCH = 38.33e6 + 1795.51e6
+TRAFFIC_PER_LAUNCH = 38.18e6 + 1738.09e6
 # Executed work per (window, group) item of that sweep, from the same capture (d = 1/2):
 # widening products = 2 per window + 14 per Philox block x 3.03 blocks (4 FMA-heavy cycles per
-# warp instruction), 22.8 other multiply-adds (2 cycles), 30.32 active lanes per warp
+# warp instruction), 11.6 other multiply-adds (2 cycles), 29.86 active lanes per warp
 # instruction, 1.2% of windows recomputed in tile halos.  Used to predict the FMA-heavy pipe's
 # activity from the timed rate, for comparison with ncu's.
 EXEC_WIDE_PER_ITEM = 2.0 + 14.0 * 3.03
-EXEC_IMAD_PER_ITEM = 22.8
-EXEC_ACTIVE_LANES = 30.32
+EXEC_IMAD_PER_ITEM = 11.6
+EXEC_ACTIVE_LANES = 29.86
 EXEC_HALO = 1.012
 UNIT = "attempts/s"
 
