@@ -221,3 +221,13 @@ def test_noalloc_binding_refuses_bad_buffers_before_any_launch():
     with pytest.raises(pcpd.PcpdError) as e:
         pcpd.sweep_noalloc(cpu, ok, L, S, 0.1, 0.5, 1, 0, 5)
     assert "CUDA" in str(e.value)
+
+
+def test_pair_density_entry_point_checks_its_arguments(lib):
+    """pcpd_pair_density (Sec. 5.3's pair density, exported so the binding only marshals) is
+    reachable through ctypes and refuses a missing handle or output before touching a device."""
+    from paper_1301_6082_gb300 import pcpd
+    out = (C.c_double * 4)()
+    assert lib.pcpd_pair_density(None, out, 4) == pcpd.PCPD_EINVAL
+    assert lib.pcpd_pair_density(None, None, 0) == pcpd.PCPD_EINVAL
+    assert "NULL" in lib.pcpd_last_error().decode()
