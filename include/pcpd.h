@@ -267,6 +267,17 @@ int pcpd_batch_run(pcpd_batch_t *b);
 /* Number of instances added. */
 size_t pcpd_batch_size(const pcpd_batch_t *b);
 
+/* Runtime-specialised kernels for members that share a threshold pair (T_D, T_DA) and window
+ * width, e.g. the seeds of one p in a near-critical sweep: such members run in launches of
+ * their own with the engine compiled for their pair (as a lone instance's long run is), the
+ * rest on the generic kernel.  mode > 0: for every pair two or more members share; 0 (the
+ * default): when those members' work reaches 2e13 attempted updates (the compile, about 1.5 s
+ * once per process and pair, then pays); < 0: never.  Changes no result bit.  Call before
+ * pcpd_batch_run; pcpd_batch_jit_launches reports how many launches of the last run used a
+ * runtime-compiled kernel (0 where no runtime compiler is available). */
+int pcpd_batch_set_jit(pcpd_batch_t *b, int mode);
+size_t pcpd_batch_jit_launches(const pcpd_batch_t *b);
+
 /* Record counts of instance i (occupied (site, sample) pairs, n <= its n_times). */
 int pcpd_batch_counts(const pcpd_batch_t *b, size_t i, uint64_t *counts_out, size_t n);
 

@@ -28,6 +28,9 @@ JIT_ENTRY = """
 extern "C" __global__ void __launch_bounds__(pcpdk::kSweepThreads, 1) pcpd_jit_sweep(const pcpdk::BatchParams B) {
   pcpdk::sweep_body<false, PCPD_JIT_W>(B);
 }
+extern "C" __global__ void __launch_bounds__(pcpdk::kSweepThreads, 1) pcpd_jit_sweep_batch(const pcpdk::BatchParams B) {
+  pcpdk::sweep_body<true, PCPD_JIT_W>(B);
+}
 """
 
 

@@ -258,7 +258,10 @@ struct JitApi {
   nvrtcResult (*cubin_size)(nvrtcProgram, size_t *);
   nvrtcResult (*cubin)(nvrtcProgram, char *);
   nvrtcResult (*destroy)(nvrtcProgram *);
+  nvrtcResult (*add_name)(nvrtcProgram, const char *);
+  nvrtcResult (*lowered_name)(nvrtcProgram, const char *, const char **);
   CUresult (*load)(CUmodule *, const void *);
+  CUresult (*get_global)(CUdeviceptr *, size_t *, CUmodule, const char *);
   CUresult (*get_fn)(CUfunction *, CUmodule, const char *);
   CUresult (*get_attr)(int *, CUfunction_attribute, CUfunction);
   CUresult (*set_attr)(CUfunction, CUfunction_attribute, int);
@@ -270,7 +273,14 @@ struct JitApi {
 std::mutex g_jit_mu;
 JitApi g_jit_api;
 bool g_jit_api_tried = false;
-std::map<std::tuple<int, uint32_t, uint32_t, uint32_t>, CUfunction> g_jit;
+// One runtime-compiled module: the single-instance entry, the batched entry (descriptors from
+// the module's own constant table) and that table's device address.
+struct JitEntry {
+  CUfunction fn = nullptr, fn_batch = nullptr;
+  CUdeviceptr c_inst = 0;
+  size_t c_inst_bytes = 0;
+};
+std::map<std::tuple<int, uint32_t, uint32_t, uint32_t>, JitEntry> g_jit;
 
 template <typename F>
 bool driver_fn(const char *name, F *out) {
@@ -303,7 +313,10 @@ const JitApi &jit_api() {   // call with g_jit_mu held
   sym("nvrtcGetCUBINSize", &a.cubin_size);
   sym("nvrtcGetCUBIN", &a.cubin);
   sym("nvrtcDestroyProgram", &a.destroy);
+  sym("nvrtcAddNameExpression", &a.add_name);
+  sym("nvrtcGetLoweredName", &a.lowered_name);
   ok = ok && driver_fn("cuModuleLoadData", &a.load) && driver_fn("cuModuleGetFunction", &a.get_fn) &&
+       driver_fn("cuModuleGetGlobal", &a.get_global) &&
        driver_fn("cuFuncGetAttribute", &a.get_attr) && driver_fn("cuFuncSetAttribute", &a.set_attr) &&
        driver_fn("cuOccupancyMaxActiveBlocksPerMultiprocessor", &a.occupancy) &&
        driver_fn("cuLaunchKernel", &a.launch);
@@ -313,8 +326,8 @@ const JitApi &jit_api() {   // call with g_jit_mu held
 }
 
 // Compile (once per device, threshold pair and window width) the engine with the thresholds
-// and the window width as constants.
-int jit_function(uint32_t td, uint32_t tda, uint32_t W, CUfunction *out) {
+// and the window width as constants: the single-instance and the batched entry of one module.
+int jit_entry(uint32_t td, uint32_t tda, uint32_t W, const JitEntry **out) {
 #ifdef PCPD_DEBUG
   (void)td, (void)tda, (void)W, (void)out;
   return fail(PCPD_ECUDA, "debug builds run the generic sweep only (its checks live in this library)");
@@ -328,12 +341,14 @@ int jit_function(uint32_t td, uint32_t tda, uint32_t W, CUfunction *out) {
   auto key = std::make_tuple(dev, td, tda, W);
   auto it = g_jit.find(key);
   if (it != g_jit.end()) {
-    *out = it->second;
+    *out = &it->second;
     return PCPD_OK;
   }
   nvrtcProgram prog;
   if (J.create(&prog, kJitSource, "pcpd_jit.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS)
     return fail(PCPD_ECUDA, "nvrtcCreateProgram failed");
+  static const char kTableExpr[] = "&pcpdk::c_inst";
+  J.add_name(prog, kTableExpr);
   char dtd[64], dtda[64], dw[32];
   snprintf(dtd, sizeof dtd, "-DPCPD_JIT_TD=0x%08xu", td);
   snprintf(dtda, sizeof dtda, "-DPCPD_JIT_TDA=0x%08xu", tda);
@@ -348,23 +363,40 @@ int jit_function(uint32_t td, uint32_t tda, uint32_t W, CUfunction *out) {
     J.destroy(&prog);
     return fail(PCPD_ECUDA, "runtime compile failed (%d): %.300s", (int)rc, log.c_str());
   }
+  const char *lowered = nullptr;
+  std::string table_name;
+  if (J.lowered_name(prog, kTableExpr, &lowered) == NVRTC_SUCCESS && lowered) table_name = lowered;
   size_t cb = 0;
   J.cubin_size(prog, &cb);
   std::vector<char> cubin(cb);
   J.cubin(prog, cubin.data());
   J.destroy(&prog);
   CUmodule mod = nullptr;
-  CUfunction fn = nullptr;
-  if (J.load(&mod, cubin.data()) != CUDA_SUCCESS || J.get_fn(&fn, mod, "pcpd_jit_sweep") != CUDA_SUCCESS)
+  JitEntry e;
+  if (J.load(&mod, cubin.data()) != CUDA_SUCCESS || J.get_fn(&e.fn, mod, "pcpd_jit_sweep") != CUDA_SUCCESS ||
+      J.get_fn(&e.fn_batch, mod, "pcpd_jit_sweep_batch") != CUDA_SUCCESS)
     return fail(PCPD_ECUDA, "loading the runtime-compiled sweep failed");
+  if (table_name.empty() || J.get_global(&e.c_inst, &e.c_inst_bytes, mod, table_name.c_str()) != CUDA_SUCCESS)
+    e.fn_batch = nullptr;   // no descriptor table: batches keep the generic kernel
   int optin = 0, stat = 0;
   int rc2 = smem_optin(&optin);
   if (rc2) return rc2;
-  J.get_attr(&stat, CU_FUNC_ATTRIBUTE_SHARED_SIZE_BYTES, fn);
-  if (J.set_attr(fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, optin - stat) != CUDA_SUCCESS)
-    return fail(PCPD_ECUDA, "setting the shared-memory limit of the runtime-compiled sweep failed");
-  g_jit[key] = fn;   // modules stay loaded until the process exits
-  *out = fn;
+  for (CUfunction f : {e.fn, e.fn_batch}) {
+    if (!f) continue;
+    J.get_attr(&stat, CU_FUNC_ATTRIBUTE_SHARED_SIZE_BYTES, f);
+    if (J.set_attr(f, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, optin - stat) != CUDA_SUCCESS)
+      return fail(PCPD_ECUDA, "setting the shared-memory limit of the runtime-compiled sweep failed");
+  }
+  auto ins = g_jit.emplace(key, e);   // modules stay loaded until the process exits
+  *out = &ins.first->second;
+  return PCPD_OK;
+}
+
+int jit_function(uint32_t td, uint32_t tda, uint32_t W, CUfunction *out) {
+  const JitEntry *e = nullptr;
+  const int rc = jit_entry(td, tda, W, &e);
+  if (rc) return rc;
+  *out = e->fn;
   return PCPD_OK;
 }
 
@@ -1215,6 +1247,8 @@ struct pcpd_batch {
   size_t items_cap = 0;
   uint32_t *d_ctl = nullptr;   // work counter, error word
   bool ran = false;
+  int jit = 0;                 // see pcpd_batch_set_jit
+  size_t jit_launches = 0;
   GraphCache gc;
 };
 
@@ -1236,8 +1270,16 @@ struct MultiTarget {
 // Advance every target in engine launches of at most kMaxBatchInst instances each; the item
 // list starts every segmented chain at once and spreads the whole-ring items (longest first)
 // between its epochs.  Waits for completion; updates each handle's buffer and clock.
+// Members of a batch that share a threshold pair and window width whose work reaches this many
+// attempted updates run a kernel compiled for that pair (as a lone instance does); below it the
+// compile (about 1.5 s, once per process and pair) would cost more than it saves.
+constexpr double kJitBatchMinAttempts = 2e13;
+
+// jit_mode: > 0 compile for every pair two or more members share, 0 when their work reaches
+// kJitBatchMinAttempts, < 0 never.  *jit_launches (nullable) counts the launches that ran a
+// runtime-compiled kernel.
 int run_multi(cudaStream_t stream, uint32_t *d_ctl, unsigned long long **d_items, size_t *items_cap,
-              std::vector<MultiTarget> &tg, GraphCache &gc) {
+              std::vector<MultiTarget> &tg, GraphCache &gc, int jit_mode = -1, size_t *jit_launches = nullptr) {
   int dev = 0, sms = 0, optin = 0;
   CU(cudaGetDevice(&dev));
   CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -1255,15 +1297,62 @@ int run_multi(cudaStream_t stream, uint32_t *d_ctl, unsigned long long **d_items
     while (rj < tg[i].rec_sub.size() && tg[i].rec_sub[rj] <= tg[i].n_end) ++rj;
     tg[i].rec_taken = rj - tg[i].rec_first;
   }
+  // Launch chunks of at most kMaxBatchInst members: first the members that share a threshold
+  // pair (and window width) worth a runtime-compiled kernel, one pair per chunk; then the rest,
+  // in order, on the generic kernel.  The grouping changes no result bit.
+  struct Chunk {
+    std::vector<size_t> ids;
+    const JitEntry *jit = nullptr;
+  };
+  std::vector<Chunk> chunks;
+  {
+    std::map<std::tuple<uint32_t, uint32_t, uint32_t>, std::vector<size_t>> groups;
+    std::vector<size_t> rest;
+    for (size_t i = 0; i < n; ++i) {
+      const pcpd_t *h = tg[i].h;
+      const bool normal = !h->T.td_full && !h->T.tda_full && h->T.td != 0u && h->T.tda != 0u;
+      if (jit_mode >= 0 && normal && epochs[i] > 0) groups[std::make_tuple(h->W, h->T.td, h->T.tda)].push_back(i);
+      else rest.push_back(i);
+    }
+    for (auto &g : groups) {
+      double work = 0.0;
+      for (size_t i : g.second) work += (double)tg[i].h->S * tg[i].h->K * (double)(tg[i].n_end - tg[i].h->n_now);
+      const JitEntry *e = nullptr;
+      bool use = g.second.size() >= 2 && (jit_mode > 0 || work >= kJitBatchMinAttempts);
+      if (use && (jit_entry(std::get<1>(g.first), std::get<2>(g.first), std::get<0>(g.first), &e) != PCPD_OK ||
+                  !e->fn_batch)) {
+        g_err.clear();   // no runtime compiler: the generic kernel runs these members
+        use = false;
+      }
+      if (!use) {
+        rest.insert(rest.end(), g.second.begin(), g.second.end());
+        continue;
+      }
+      for (size_t c0 = 0; c0 < g.second.size(); c0 += pcpdk::kMaxBatchInst) {
+        Chunk ch;
+        ch.ids.assign(g.second.begin() + c0,
+                      g.second.begin() + std::min(g.second.size(), c0 + (size_t)pcpdk::kMaxBatchInst));
+        ch.jit = e;
+        chunks.push_back(std::move(ch));
+      }
+    }
+    std::sort(rest.begin(), rest.end());
+    for (size_t c0 = 0; c0 < rest.size(); c0 += pcpdk::kMaxBatchInst) {
+      Chunk ch;
+      ch.ids.assign(rest.begin() + c0, rest.begin() + std::min(rest.size(), c0 + (size_t)pcpdk::kMaxBatchInst));
+      chunks.push_back(std::move(ch));
+    }
+  }
   std::lock_guard<std::mutex> lock(g_batch_mu);
-  for (size_t c0 = 0; c0 < n; c0 += pcpdk::kMaxBatchInst) {
-    const size_t c1 = std::min(n, c0 + (size_t)pcpdk::kMaxBatchInst);
-    std::vector<pcpdk::InstDesc> desc(c1 - c0);
+  for (const Chunk &ch : chunks) {
+    const std::vector<size_t> &ids = ch.ids;
+    std::vector<pcpdk::InstDesc> desc(ids.size());
     size_t tile_words = 0;
     uint32_t threads = 64;   // the launch takes the largest CTA any member's plan asks for
-    for (size_t i = c0; i < c1; ++i) {
+    for (size_t q = 0; q < ids.size(); ++q) {
+      const size_t i = ids[q];
       pcpd_t *h = tg[i].h;
-      fill_desc(h, desc[i - c0], h->n_now, tg[i].n_end, tg[i].rec_first, tg[i].rec_first + tg[i].rec_taken,
+      fill_desc(h, desc[q], h->n_now, tg[i].n_end, tg[i].rec_first, tg[i].rec_first + tg[i].rec_taken,
                 tg[i].slot0);
       tile_words = std::max(tile_words, h->tile_words);
       threads = std::max(threads, h->threads);
@@ -1271,14 +1360,15 @@ int run_multi(cudaStream_t stream, uint32_t *d_ctl, unsigned long long **d_items
     std::vector<std::pair<double, unsigned long long>> ring_items;
     std::vector<unsigned long long> items;
     uint64_t max_ep = 0;
-    for (size_t i = c0; i < c1; ++i) max_ep = std::max(max_ep, tg[i].h->ring ? 0 : epochs[i]);
-    for (size_t i = c0; i < c1; ++i) {
+    for (size_t i : ids) max_ep = std::max(max_ep, tg[i].h->ring ? 0 : epochs[i]);
+    for (size_t q = 0; q < ids.size(); ++q) {
+      const size_t i = ids[q];
       pcpd_t *h = tg[i].h;
       if (!h->ring) continue;
       for (uint64_t e = 0; e < epochs[i]; ++e) {
         const uint64_t len = std::min<uint64_t>(h->tau, tg[i].n_end - h->n_now - e * h->tau);
         for (uint32_t t = 0; t < h->tiles; ++t)
-          ring_items.push_back({-(double)h->gpi * h->K * (double)len, pcpdk::pack_item((uint32_t)(i - c0), (uint32_t)e, t)});
+          ring_items.push_back({-(double)h->gpi * h->K * (double)len, pcpdk::pack_item((uint32_t)q, (uint32_t)e, t)});
       }
     }
     // longest first; a later epoch of a tile sorts after all earlier epochs
@@ -1295,10 +1385,11 @@ int run_multi(cudaStream_t stream, uint32_t *d_ctl, unsigned long long **d_items
     };
     for (uint64_t e = 0; e < max_ep; ++e) {
       if (e > 0) add_ring(per_round);
-      for (size_t i = c0; i < c1; ++i) {
+      for (size_t q = 0; q < ids.size(); ++q) {
+        const size_t i = ids[q];
         pcpd_t *h = tg[i].h;
         if (h->ring || e >= epochs[i]) continue;
-        for (uint32_t t = 0; t < h->tiles; ++t) items.push_back(pcpdk::pack_item((uint32_t)(i - c0), (uint32_t)e, t));
+        for (uint32_t t = 0; t < h->tiles; ++t) items.push_back(pcpdk::pack_item((uint32_t)q, (uint32_t)e, t));
       }
     }
     add_ring(ring_items.size());
@@ -1344,22 +1435,43 @@ int run_multi(cudaStream_t stream, uint32_t *d_ctl, unsigned long long **d_items
     for (const pcpdk::InstDesc &dd : desc)
       if (dd.W != wfix) wfix = 0u;
     const SweepKernel kern = sweep_kernel(true, wfix);
-    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, dyn));
+    const JitEntry *jit = ch.jit;
+    if (jit) {
+      if (g_jit_api.occupancy(&per_sm, jit->fn_batch, (int)threads, dyn) != CUDA_SUCCESS) per_sm = 0;
+      if (per_sm < 1) jit = nullptr;   // the generic kernel then
+    }
+    if (!jit) CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, dyn));
     if (per_sm < 1) return fail(PCPD_EINVAL, "batch plan does not fit one CTA per SM");
     const int grid = (int)std::min<uint64_t>((uint64_t)per_sm * sms, items.size());
     // capture the round, then update the cached executable graph (or instantiate it)
     CU(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
     cudaMemcpyAsync(*d_items, gc.h_items, items.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice, stream);
-    cudaMemcpyToSymbolAsync(pcpdk::c_inst, gc.h_desc, desc.size() * sizeof(pcpdk::InstDesc), 0,
-                            cudaMemcpyHostToDevice, stream);
+    if (jit)   // the runtime-compiled module has its own descriptor table
+      cudaMemcpyAsync((void *)jit->c_inst, gc.h_desc, desc.size() * sizeof(pcpdk::InstDesc), cudaMemcpyHostToDevice,
+                      stream);
+    else
+      cudaMemcpyToSymbolAsync(pcpdk::c_inst, gc.h_desc, desc.size() * sizeof(pcpdk::InstDesc), 0,
+                              cudaMemcpyHostToDevice, stream);
     cudaMemsetAsync(d_ctl, 0, sizeof(uint32_t), stream);   // work counter
-    kern<<<grid, threads, dyn, stream>>>(B);
+    CUresult launch_rc = CUDA_SUCCESS;
+    if (jit) {
+      void *args[] = {&B};
+      launch_rc = g_jit_api.launch(jit->fn_batch, grid, 1, 1, threads, 1, 1, (unsigned)dyn, (CUstream)stream, args,
+                                   nullptr);
+    } else {
+      kern<<<grid, threads, dyn, stream>>>(B);
+    }
     cudaGraph_t graph = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(stream, &graph);
     if (ec != cudaSuccess) {
       if (graph) cudaGraphDestroy(graph);
       return fail(PCPD_ECUDA, "graph capture: %s", cudaGetErrorString(ec));
     }
+    if (launch_rc != CUDA_SUCCESS) {
+      cudaGraphDestroy(graph);
+      return fail(PCPD_ECUDA, "launch of the runtime-compiled batch sweep failed (%d)", (int)launch_rc);
+    }
+    if (jit && jit_launches) ++*jit_launches;
     bool updated = false;
     if (gc.exec) {
       cudaGraphExecUpdateResultInfo info;
@@ -1487,7 +1599,8 @@ int pcpd_batch_run(pcpd_batch_t *b) {
     tg[i].rec_first = 0;
     tg[i].slot0 = 0;
   }
-  int rc = run_multi(b->stream, b->d_ctl, &b->d_items, &b->items_cap, tg, b->gc);
+  b->jit_launches = 0;
+  int rc = run_multi(b->stream, b->d_ctl, &b->d_items, &b->items_cap, tg, b->gc, b->jit, &b->jit_launches);
   if (rc) return rc;
   for (size_t i = 0; i < n; ++i) {
     pcpd_t *h = b->inst[i];
@@ -1516,6 +1629,14 @@ int pcpd_batch_lattice(const pcpd_batch_t *b, size_t i, uint32_t *host_out) {
 }
 
 size_t pcpd_batch_size(const pcpd_batch_t *b) { return b ? b->inst.size() : 0; }
+
+int pcpd_batch_set_jit(pcpd_batch_t *b, int mode) {
+  if (!b) return fail(PCPD_EINVAL, "NULL batch");
+  b->jit = mode > 0 ? 1 : (mode < 0 ? -1 : 0);
+  return PCPD_OK;
+}
+
+size_t pcpd_batch_jit_launches(const pcpd_batch_t *b) { return b ? b->jit_launches : 0; }
 
 }  // extern "C"
 

@@ -96,6 +96,8 @@ SIGNATURES = [
     ("pcpd_batch_add", C.c_int, [C.c_void_p, C.POINTER(Params), C.c_uint64, _u64p, C.c_size_t, C.POINTER(C.c_size_t)]),
     ("pcpd_batch_run", C.c_int, [C.c_void_p]),
     ("pcpd_batch_size", C.c_size_t, [C.c_void_p]),
+    ("pcpd_batch_set_jit", C.c_int, [C.c_void_p, C.c_int]),
+    ("pcpd_batch_jit_launches", C.c_size_t, [C.c_void_p]),
     ("pcpd_batch_counts", C.c_int, [C.c_void_p, C.c_size_t, _u64p, C.c_size_t]),
     ("pcpd_batch_lattice", C.c_int, [C.c_void_p, C.c_size_t, _u32p]),
     ("pcpd_batch_pair_counts", C.c_int, [C.c_void_p, C.c_size_t, _u64p, C.c_size_t]),
@@ -332,6 +334,15 @@ class Batch:
                                      t.size, C.byref(idx)))
         self._meta.append((L, samples, len(t)))
         return int(idx.value)
+
+    def set_jit(self, mode: int):
+        """Runtime-specialised kernels for members sharing a threshold pair: 1 always, 0 when
+        their work is large enough, -1 never (include/pcpd.h, pcpd_batch_set_jit)."""
+        _check(load().pcpd_batch_set_jit(self._h, mode))
+
+    @property
+    def jit_launches(self) -> int:
+        return int(load().pcpd_batch_jit_launches(self._h))
 
     def run(self):
         _check(load().pcpd_batch_run(self._h))

@@ -109,3 +109,40 @@ def test_batch_errors(P):
     with pytest.raises(P.PcpdError):
         b.run()
     b.close()
+
+
+def test_members_sharing_thresholds_run_a_specialised_kernel(P, oracle_mod):
+    """Members that share (T_D, T_DA) and window width (the seeds of one p in a sweep) run in
+    launches of the engine compiled for their pair; the rest on the generic kernel.  Same bits
+    either way, and the same as the oracle."""
+    spec = [  # L, S, p, d, seed, mcs, init, tuple
+        (3000, 64, 0.15, 0.5, 21, 30, INIT_HALF, 2),
+        (65536, 64, 0.15, 0.5, 22, 4, INIT_FULL, 2),   # segmented, same pair as the first
+        (1000, 96, 0.15, 0.5, 23, 40, INIT_HALF, 2),
+        (2000, 64, 0.2, 0.3, 24, 25, INIT_HALF, 2),     # a pair of its own
+        (3001, 32, 0.15, 0.5, 25, 30, INIT_HALF, 3),    # same pair, other window width
+        (3001, 32, 0.15, 0.5, 26, 30, INIT_FULL, 3),
+    ]
+    lattices = {}
+    for mode in (1, -1):
+        b = P.Batch()
+        b.set_jit(mode)
+        ids = []
+        for L, S, p, d, seed, mcs, init, tup in spec:
+            ids.append(b.add(L, S, p, d, seed, mcs, [mcs // 2, mcs], init=init, tuple_n=tup))
+        b.run()
+        if mode > 0:
+            assert b.jit_launches == 2, b.jit_launches    # the PCPD pair and the TCPD pair
+        else:
+            assert b.jit_launches == 0
+        lattices[mode] = [(b.counts(i), b.lattice(i)) for i in ids]
+        b.close()
+    for (c1, l1), (c2, l2) in zip(lattices[1], lattices[-1]):
+        np.testing.assert_array_equal(c1, c2)
+        np.testing.assert_array_equal(l1, l2)
+    for (L, S, p, d, seed, mcs, init, tup), (c, lat) in zip(spec, lattices[1]):
+        subs = [oracle_mod.substep_of_time(L, t, tup) for t in (mcs // 2, mcs)]
+        st = oracle_mod.init_state(L, S, init, seed)
+        tot, _, _ = oracle_mod.run(st, p, d, seed, 0, subs[-1], subs, tuple_n=tup)
+        np.testing.assert_array_equal(c, tot)
+        np.testing.assert_array_equal(lat, oracle_mod.pack(st))
