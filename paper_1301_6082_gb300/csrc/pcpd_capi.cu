@@ -493,8 +493,21 @@ int make_plan(pcpd_t *h, const pcpd_params *prm, PlanMode mode = kPlanOne) {
         if (core <= max_core) break;   // the rounding may push a tile past the budget
       }
     }
+    // A tile's halo may only reach into its two neighbours (the epoch flags it waits on), so
+    // every tile's core, the ragged last one included, must be at least a halo long.  Where the
+    // requested length leaves a short last tile, the tiles are evened out (same count, each at
+    // most the requested length, starts still 16-byte aligned).
+    uint32_t nseg_c = (L + core - 1) / core;
+    if (nseg_c >= 2 && L - (nseg_c - 1) * core < h->halo) {
+      const uint32_t even = (((L + nseg_c - 1) / nseg_c) + 3u) & ~3u;
+      if (even <= core) core = even;
+      nseg_c = (L + core - 1) / core;
+    }
+    if (nseg_c >= 2 && (core < h->halo || L - (nseg_c - 1) * core < h->halo))
+      return fail(PCPD_EINVAL, "segment tiles of %u sites (last %u) are shorter than the halo of %u sites", core,
+                  L - (nseg_c - 1) * core, h->halo);
     h->core = core;
-    h->n_seg = (L + core - 1) / core;
+    h->n_seg = nseg_c;
     h->tile_words = (size_t)core + 2u * h->halo;
     if (h->tile_words > avail_words) return fail(PCPD_EINVAL, "tile of %zu sites exceeds shared memory", h->tile_words);
     // a tile shorter than L - 4W sees fewer candidate windows than the ring has

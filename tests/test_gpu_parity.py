@@ -454,3 +454,27 @@ def test_tile_count_limit_is_enforced(P):
     with pytest.raises(P.PcpdError) as e:
         P.Pcpd(1 << 22, 1 << 22, 0.1, 0.1, plan_seg_sites=1024, plan_tau=16)
     assert e.value.code == P.PCPD_EINVAL and "tiles" in str(e.value)
+
+
+def test_no_tile_is_shorter_than_its_halo(P, oracle_mod):
+    """A tile's halo may reach only into its two neighbours, whose epoch flags it waits on; a
+    ragged last tile shorter than the halo (L = 3001 in tiles of 1000: a 1-site last tile)
+    would let a halo reach two tiles away and race with a tile it does not wait for.  The
+    planner evens such tiles out (4 tiles of at most 752 sites) and refuses tiles that cannot
+    hold a halo; the evened plan runs several epochs bit-exact to the oracle."""
+    L, S, p, d, seed = 3001, 64, 0.15, 0.5, 31
+    a = P.Pcpd(L, S, p, d, seed=seed, init=INIT_HALF, plan_seg_sites=1000, plan_tau=20, jit=-1)
+    plan = a.plan()
+    assert plan["ring"] == 0 and plan["n_seg"] == 4 and plan["core"] == 752, plan
+    assert L - 3 * plan["core"] >= plan["halo"]
+    ts = [5, 30, 60]
+    a.run(ts[-1], ts)
+    subs = [oracle_mod.substep_of_time(L, t) for t in ts]
+    st = oracle_mod.init_state(L, S, INIT_HALF, seed)
+    tot, _, _ = oracle_mod.run(st, p, d, seed, 0, subs[-1], subs)
+    np.testing.assert_array_equal(a.counts(), tot)
+    np.testing.assert_array_equal(a.lattice(), oracle_mod.pack(st))
+    a.close()
+    with pytest.raises(P.PcpdError) as e:
+        P.Pcpd(3000, 64, p, d, plan_seg_sites=40, plan_tau=20, jit=-1)
+    assert e.value.code == P.PCPD_EINVAL and "halo" in str(e.value)
