@@ -69,7 +69,10 @@ typedef struct pcpd_params {
        tile, whole-column or not, sized for two CTAs of at most 256 threads per SM, so that a
        launch of any mix of members runs two CTAs per SM). */
     uint32_t plan_threads;   /* threads per CTA (multiple of 32 in [64, 512]) */
-    uint32_t plan_seg_sites; /* core sites per tile for lattices that do not fit one CTA */
+    uint32_t plan_seg_sites; /* core sites per tile for lattices that do not fit one CTA (at
+                                most; every tile, the last included, must be at least a halo
+                                long: a short last tile evens the tiles out, a length below
+                                the halo is refused) */
     uint32_t plan_tau;       /* sub-steps per tile residency (temporal block) */
     int autotune;            /* non-zero and no plan_* override: use the plan pcpd_autotune
                                 picks for this (L, samples), tuning on first use */
