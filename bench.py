@@ -515,7 +515,7 @@ def compact(d, keys):
 
 def compact_roofline(r):
     """The roofline entries the headline line carries; the notes go to the detail line."""
-    keep = ("bound", "achieved", "peak", "unit", "frac", "traffic", "binding_pipe", "frac_logic_pipe",
+    keep = ("bound", "achieved", "peak", "unit", "frac", "traffic", "frac_logic_pipe",
             "frac_of_issue_slots", "peak_measured", "fmaheavy_active_pred")
     out = {k: r[k] for k in keep if k in r}
     for k in ("achieved", "peak", "frac", "frac_logic_pipe", "frac_of_issue_slots", "peak_measured",
@@ -745,10 +745,12 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
                 "config": {"workload": W["name"], "L": L, "samples": S, "runs_d_p": [list(r) for r in runs],
-                           "mcs_per_step": mcs, "l2": "inputs larger than L2 (192 MiB of lattices)",
-                           "parallelism": f"group shards x{world}"},
-                "roofline": compact_roofline(roofline), "cpu_baseline": compact(cpu, ("value", "unit", "cores", "host_cores", "kind", "sample")),
-                "e2e": compact(e2e, ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step")), "clocks": clk,
+                           "mcs_per_step": mcs, "l2": "inputs > L2", "parallelism": f"group shards x{world}"},
+                "roofline": compact_roofline(roofline),
+                "cpu_baseline": None if cpu is None else dict(compact(cpu, ("value", "unit", "cores", "host_cores", "kind")),
+                                                              sample=cpu["sample"].split(" (")[0]),
+                "e2e": compact(e2e, ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step")),
+                "clocks": compact(clk, ("sm_mhz", "sm_max_mhz", "reasons")),
                 "gpu_launches": launches,
                 "batch": compact(batch, ("speedup", "batched", "plain", "results_identical")),
                 "serving": None if serving is None else {
@@ -756,7 +758,7 @@ def main():
                     "p99_latency_s": serving["p99_latency_s"], "at_load": serving["at_load"],
                     "curve": [[c["load"], round(c["throughput"] / 1e12, 3), round(c["p50_latency_s"], 4),
                                round(c["p99_latency_s"], 4)] for c in serving["curve"]]}}
-        print(json.dumps(line), flush=True)
+        print(json.dumps(line, separators=(",", ":")), flush=True)
     for s in sims:
         s.close()
     if dist:
