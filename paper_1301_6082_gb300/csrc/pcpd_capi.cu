@@ -1449,6 +1449,7 @@ int run_multi(cudaStream_t stream, uint32_t *d_ctl, unsigned long long **d_items
       if (dd.W != wfix) wfix = 0u;
     const SweepKernel kern = sweep_kernel(true, wfix);
     const JitEntry *jit = ch.jit;
+    if (jit && jit->c_inst_bytes < desc.size() * sizeof(pcpdk::InstDesc)) jit = nullptr;   // table too small
     if (jit) {
       if (g_jit_api.occupancy(&per_sm, jit->fn_batch, (int)threads, dyn) != CUDA_SUCCESS) per_sm = 0;
       if (per_sm < 1) jit = nullptr;   // the generic kernel then
