@@ -59,6 +59,10 @@ UNIT = "attempts/s"
 # 32.0 products per SM and clock), and the bench re-measures the Philox rate on every run.
 LOGIC_LANES = 64
 WIDE_MUL_LANES = 32
+# Shared memory: 32 banks of 4 bytes per SM, one 128-byte wavefront per clock.  A (window,
+# group) item of the PCPD reads and writes its three words: 24 bytes.
+SMEM_BYTES_PER_CLK = 128
+SMEM_BYTES_PER_ITEM = 24
 
 
 def algorithmic_ops_per_item(t_d: int, t_da: int):
@@ -516,9 +520,9 @@ def compact(d, keys):
 def compact_roofline(r):
     """The roofline entries the headline line carries; the notes go to the detail line."""
     keep = ("bound", "achieved", "peak", "unit", "frac", "traffic", "frac_logic_pipe",
-            "frac_of_issue_slots", "peak_measured", "fmaheavy_active_pred")
+            "frac_of_issue_slots", "frac_smem", "peak_measured", "fmaheavy_active_pred")
     out = {k: r[k] for k in keep if k in r}
-    for k in ("achieved", "peak", "frac", "frac_logic_pipe", "frac_of_issue_slots", "peak_measured",
+    for k in ("achieved", "peak", "frac", "frac_logic_pipe", "frac_of_issue_slots", "frac_smem", "peak_measured",
               "fmaheavy_active_pred"):
         if isinstance(out.get(k), float):
             out[k] = round(out[k], 4)
@@ -669,6 +673,7 @@ def main():
                 "wide_multiplies_per_item": round(mul_item, 2), "logic_ops_per_item": round(logic_item, 2),
                 "expected_philox_blocks_per_item": [round(o[1], 3) for o in ops_item],
                 "frac_of_issue_slots": (alg_ops / (ms / 1e3)) / 1e12 / issue_peak,
+                "frac_smem": items_s * SMEM_BYTES_PER_ITEM / (sm_count * SMEM_BYTES_PER_CLK * sm_max_mhz * 1e6),
                 "measured_lanes_per_sm_clock": pipe_rates,
                 "fmaheavy_active_pred": items_s * (EXEC_WIDE_PER_ITEM * 4 + EXEC_IMAD_PER_ITEM * 2) / EXEC_ACTIVE_LANES
                 * EXEC_HALO / (4 * sm_count * sm_max_mhz * 1e6),
