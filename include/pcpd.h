@@ -442,8 +442,7 @@ void pcpd_paper_destroy(pcpd_paper_t *h);
  *            substep_begin + n_substeps sub-steps (bit-identical to pcpd_run_substeps).
  *   L, samples, p, d, seed   as for pcpd_create; stream: cudaStream_t or NULL.
  * The call is synchronous: it waits on `stream` after every launch to read the error word
- * into host memory, so it cannot be made while `stream` (or the legacy default stream) is
- * being captured into a CUDA graph.  Errors: PCPD_EINVAL (bad sizes or pointers, or more
+ * into host memory.  Errors: PCPD_EINVAL (bad sizes or pointers, or more
  * tiles per epoch than the scratch holds -- about 16384 columns of up to ~50k sites, fewer
  * for longer columns), PCPD_ENODEV, PCPD_ECUDA, PCPD_ETIMEOUT.  After any error the contents
  * of both lattices are undefined (a run may stop between two launches, with the newest state
