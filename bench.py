@@ -548,6 +548,8 @@ def main():
     ap.add_argument("--paper-mcs", type=int, default=1000)
     ap.add_argument("--batch-only", action="store_true",
                     help="run only the 512-instance batch leg (for profiling) and print its JSON")
+    ap.add_argument("--batch-mcs-div", type=int, default=100,
+                    help="divide every MCS count of the 512-instance mix by this (1 = the mix as specified)")
     ap.add_argument("--stream-only", action="store_true",
                     help="run only the HBM-streamed leg (for profiling) and print its JSON")
     ap.add_argument("--stream-substeps", type=int, default=2048)
@@ -569,7 +571,7 @@ def main():
         print(json.dumps({"paper_scheme": paper_leg(pcpd, mcs=args.paper_mcs)}), flush=True)
         return 0
     if args.batch_only:
-        print(json.dumps({"batch": batch_leg(pcpd)}), flush=True)
+        print(json.dumps({"batch": batch_leg(pcpd, mcs_div=max(1, args.batch_mcs_div))}), flush=True)
         return 0
     if args.stream_only:
         print(json.dumps({"streamed": stream_leg(pcpd, substeps=args.stream_substeps)}), flush=True)
