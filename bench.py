@@ -266,10 +266,21 @@ def batch_leg(pcpd, mcs_div: int = 100):
     batch_launches = pcpd.kernel_launches() - l0
     same = all(int(b.counts(i)[-1]) == int(c) for i, c in enumerate(plain_counts))
     b.close()
+    # the batched rate against the same multiply-pipe roofline as the headline sweep: each
+    # member's algorithmic widening products (its expected Philox blocks x 20 per item)
+    products = 0.0
+    for m in mix:
+        td, tda = pcpd.thresholds(m["p"], m["d"])
+        items = m["S"] // 32 * (m["L"] // 3) * pcpd.substep_of_time(m["L"], m["mcs_run"])
+        products += items * algorithmic_ops_per_item(td, tda)[3]
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    peak = props.multi_processor_count * WIDE_MUL_LANES * measured_peak("sm_max_mhz", 2070.0) * 1e6
     return {"workload": "512-instance mix, MCS/%d" % mcs_div, "attempts": attempts,
             "batched": attempts / t_batch, "plain": attempts / t_plain, "unit": UNIT,
             "speedup": t_plain / t_batch, "batched_launches": batch_launches, "plain_launches": plain_launches,
-            "results_identical": bool(same)}
+            "results_identical": bool(same), "frac": round(products / t_batch / peak, 4),
+            "frac_plain": round(products / t_plain / peak, 4),
+            "frac_note": "algorithmic widening products of every member / wall time / the headline sweep's peak"}
 
 
 def sweep_batch_leg(pcpd, mcs: int = 300):
@@ -759,7 +770,7 @@ def main():
                 "e2e": compact(e2e, ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step")),
                 "clocks": compact(clk, ("sm_mhz", "sm_max_mhz", "reasons")),
                 "gpu_launches": launches,
-                "batch": compact(batch, ("speedup", "batched", "plain", "results_identical")),
+                "batch": compact(batch, ("speedup", "batched", "plain", "results_identical", "frac")),
                 "serving": None if serving is None else {
                     "capacity": serving["capacity"], "p50_latency_s": serving["p50_latency_s"],
                     "p99_latency_s": serving["p99_latency_s"], "at_load": serving["at_load"],
